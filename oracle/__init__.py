@@ -1,0 +1,200 @@
+"""CPU FP64 oracle for the matricized least-square-errors polynomial fit.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this package.  It shares no
+code with the CUDA library and never calls it; the library never calls this.
+
+The arithmetic lives in ``lsefit_oracle.c`` (plain sequential C, FP64, every
+operation separately rounded), which follows Section II of Dasgupta,
+arXiv 1512.08017: the power sums S_k = sum x^k (k <= 2m) and
+T_k = sum x^k y (k <= m), the Hankel normal matrix A[j][k] = S_{j+k},
+B[j] = T_j, and Gaussian elimination of AX = B.  Two independent validators
+sit beside it: ``exact`` (the same definition in exact rational arithmetic)
+and ``householder`` (the Vandermonde QR least-squares solve that Section III
+describes for MATLAB's polyfit).
+
+Readings where the paper is silent or misprinted are listed at the top of
+``lsefit_oracle.c``.  Parity unpinned: the correlation coefficient "R" of
+Tables II-IV (the paper does not define it) is not part of the oracle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+# LSEFIT_ORACLE_SOURCE lets the mutation tests build the oracle from a copy of
+# lsefit_oracle.c with a planted mistake (in a separate process and build dir).
+_SRC = os.environ.get("LSEFIT_ORACLE_SOURCE") or os.path.join(_HERE, "lsefit_oracle.c")
+_BUILD_DIR = os.environ.get("LSEFIT_ORACLE_BUILD_DIR") or os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "liblsefit_oracle.so")
+
+# Oracle status values, as numbered in lsefit_oracle.c.
+STATUS_NAMES = {0: "ok", 1: "n_too_small", 2: "singular", 3: "nonfinite",
+                4: "bad_interval", 5: "bad_arg"}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile lsefit_oracle.c into a shared library (gcc, -O2, no FMA contraction)."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["cc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c99",
+           "-Wall", "-Werror", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        i64 = ctypes.c_int64
+        lib.orc_map_constants.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, dp]
+        lib.orc_map_constants.restype = ctypes.c_int
+        lib.orc_powersums.argtypes = [dp, dp, i64, ctypes.c_int, dp, dp, dp]
+        lib.orc_powersums.restype = None
+        lib.orc_solve.argtypes = [ctypes.c_int, dp, dp, dp]
+        lib.orc_solve.restype = ctypes.c_int
+        lib.orc_unmap.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp]
+        lib.orc_unmap.restype = None
+        lib.orc_fit.argtypes = [dp, dp, i64, ctypes.c_int, dp, dp, dp, dp, dp]
+        lib.orc_fit.restype = ctypes.c_int
+        lib.orc_eval.argtypes = [ctypes.c_int, dp, dp, i64, dp]
+        lib.orc_eval.restype = None
+        lib.orc_sse.argtypes = [ctypes.c_int, dp, dp, dp, i64]
+        lib.orc_sse.restype = ctypes.c_double
+        lib.orc_backward.argtypes = [dp, dp, i64, ctypes.c_int, dp, dp, dp, dp, dp, dp]
+        lib.orc_backward.restype = ctypes.c_int
+        lib.orc_max_degree.argtypes = []
+        lib.orc_max_degree.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def max_degree() -> int:
+    return _load().orc_max_degree()
+
+
+def map_constants(lo: float, hi: float, fp32: bool):
+    """(c, s) of the affine map t = s(x - c) onto [-1, 1]; rounded to FP32 if fp32.
+
+    Returns (status_name, c, s)."""
+    c = ctypes.c_double(0.0)
+    s = ctypes.c_double(0.0)
+    st = _load().orc_map_constants(float(lo), float(hi), int(bool(fp32)),
+                                   ctypes.byref(c), ctypes.byref(s))
+    return STATUS_NAMES[st], c.value, s.value
+
+
+def powersums(x, y, m: int, cs=None):
+    """S[0..2m], T[0..m] of Section II (t = s(x - c) when cs = (c, s) is given)."""
+    x = _f64(x)
+    y = _f64(y)
+    assert x.shape == y.shape and x.ndim == 1
+    S = np.zeros(2 * m + 1)
+    T = np.zeros(m + 1)
+    mp = _f64(cs) if cs is not None else None
+    _load().orc_powersums(_ptr(x), _ptr(y), x.size, m, _ptr(mp) if mp is not None else None,
+                          _ptr(S), _ptr(T))
+    return S, T
+
+
+def solve(S, T, m: int):
+    """Gaussian elimination (partial pivoting) of A X = B built from S, T.
+
+    Returns (status_name, X)."""
+    S = _f64(S)
+    T = _f64(T)
+    X = np.full(m + 1, np.nan)
+    st = _load().orc_solve(m, _ptr(S), _ptr(T), _ptr(X))
+    return STATUS_NAMES[st], X
+
+
+def unmap(Xt, c: float, s: float):
+    """x-basis coefficients of sum_k Xt[k] (s(x - c))^k."""
+    Xt = _f64(Xt)
+    X = np.zeros_like(Xt)
+    _load().orc_unmap(Xt.size - 1, float(c), float(s), _ptr(Xt), _ptr(X))
+    return X
+
+
+def fit(x, y, m: int, cs=None) -> dict:
+    """The paper's fit.  Returns dict(status, X, Xt, S, T)."""
+    x = _f64(x)
+    y = _f64(y)
+    assert x.shape == y.shape and x.ndim == 1
+    X = np.zeros(m + 1)
+    Xt = np.zeros(m + 1)
+    S = np.zeros(2 * m + 1)
+    T = np.zeros(m + 1)
+    mp = _f64(cs) if cs is not None else None
+    st = _load().orc_fit(_ptr(x), _ptr(y), x.size, m, _ptr(mp) if mp is not None else None,
+                         _ptr(X), _ptr(Xt), _ptr(S), _ptr(T))
+    return {"status": STATUS_NAMES[st], "X": X, "Xt": Xt, "S": S, "T": T}
+
+
+def fit_interval(x, y, m: int, lo: float, hi: float, fp32: bool) -> dict:
+    """Fit on t = s(x - c) for the map of [lo, hi] onto [-1, 1], coefficients mapped back."""
+    st, c, s = map_constants(lo, hi, fp32)
+    if st != "ok":
+        n = m + 1
+        return {"status": st, "X": np.full(n, np.nan), "Xt": np.full(n, np.nan),
+                "S": None, "T": None, "c": np.nan, "s": np.nan}
+    out = fit(x, y, m, (c, s))
+    out["c"] = c
+    out["s"] = s
+    return out
+
+
+def evaluate(X, x):
+    """f(x_i) = sum_j X[j] x_i^j."""
+    X = _f64(X)
+    x = _f64(x)
+    f = np.zeros_like(x)
+    _load().orc_eval(X.size - 1, _ptr(X), _ptr(x), x.size, _ptr(f))
+    return f
+
+
+def sse(X, x, y) -> float:
+    """sum_i (y_i - f(x_i))^2."""
+    X = _f64(X)
+    x = _f64(x)
+    y = _f64(y)
+    return float(_load().orc_sse(X.size - 1, _ptr(X), _ptr(x), _ptr(y), x.size))
+
+
+def backward(x, y, m: int, cs, S, Xt, gX):
+    """Adjoint of ``fit`` for dL/dX = gX.  Returns (status_name, dx, dy)."""
+    x = _f64(x)
+    y = _f64(y)
+    S = _f64(S)
+    Xt = _f64(Xt)
+    gX = _f64(gX)
+    dx = np.zeros_like(x)
+    dy = np.zeros_like(x)
+    mp = _f64(cs) if cs is not None else None
+    st = _load().orc_backward(_ptr(x), _ptr(y), x.size, m, _ptr(mp) if mp is not None else None,
+                              _ptr(S), _ptr(Xt), _ptr(gX), _ptr(dx), _ptr(dy))
+    return STATUS_NAMES[st], dx, dy

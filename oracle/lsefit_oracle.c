@@ -1,0 +1,293 @@
+/*
+ * lsefit_oracle.c -- plain, slow, sequential FP64 oracle for the matricized
+ * least-square-errors polynomial fit (Dasgupta, "An Analytical Evaluation of
+ * Matricizing Least-Square-Errors Curve Fitting", arXiv 1512.08017).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file exists to check the CUDA library
+ * against the paper.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load it.  It shares no code, header,
+ * table or constant with the CUDA path, and the CUDA path never calls it.
+ *
+ * Every step follows the paper's route in the paper's order:
+ *   Section II, the objective  Pi = sum_i [y_i - f(x_i)]^2  with
+ *               f(x) = a_0 + a_1 x + ... + a_m x^m;
+ *   Section II, the normal equations  sum_i x_i^j y_i = sum_k a_k sum_i x_i^(j+k);
+ *   Section II, the matrices  A (Hankel of the power sums S_0..S_2m),
+ *               B = [T_0..T_m], X = [a_0..a_m];
+ *   Section II, Gaussian elimination of AX = B.
+ * Readings where the paper is silent or misprinted:
+ *   - the derivative printed in Section II drops the factor x_i^j inside the
+ *     sum; the expanded normal equations right after it are used;
+ *   - the top-left entry of A is printed "1"; it is S_0 = n;
+ *   - the last row of A is printed with x^(m+2) in its second column; the
+ *     Hankel rule A[j][k] = S_{j+k} is used;
+ *   - "Gaussian elimination" carries no pivoting rule: partial pivoting with
+ *     the first row of largest magnitude, and a pivot below
+ *     (m+1)*eps64*max|A| reported as singular;
+ *   - n >= 2 is only enough for m = 1: n >= m+1 is required.
+ * Not in the paper (the precision extension of the method):
+ *   - an affine map t = s*(x - c) of the abscissae, with c = (lo+hi)/2 and
+ *     s = 2/(hi-lo) rounded to the precision in which the points are mapped
+ *     (FP32 for FP32/BF16 arithmetic, FP64 otherwise); the fit runs on t and
+ *     the coefficients are mapped back by the binomial expansion of
+ *     (s(x - c))^k;
+ *   - the adjoint of the fit (derived by the chain rule from the normal
+ *     equations): with lambda solving A lambda = dL/dXt,
+ *     dL/dy_i = lambda(t_i) and dL/dt_i = lambda'(t_i) r_i - lambda(t_i) f'(t_i).
+ *
+ * Build: cc -O2 -ffp-contract=off -fPIC -shared lsefit_oracle.c -lm
+ * (-ffp-contract=off keeps every product and sum a separately rounded IEEE
+ * operation on every host, so results do not depend on FMA contraction.)
+ */
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+/* Oracle status values (own numbering; the test suite maps them by name). */
+#define ORC_OK 0
+#define ORC_N_TOO_SMALL 1
+#define ORC_SINGULAR 2
+#define ORC_NONFINITE 3
+#define ORC_BAD_INTERVAL 4
+#define ORC_BAD_ARG 5
+
+#define ORC_MAX_M 16
+
+int orc_max_degree(void) { return ORC_MAX_M; }
+
+/*
+ * Map constants of the affine map onto [-1, 1].  c = (lo+hi)/2 and
+ * s = 2/(hi-lo), each rounded once to FP32 when fp32 != 0.
+ */
+int orc_map_constants(double lo, double hi, int fp32, double* c, double* s)
+{
+    if (!(isfinite(lo) && isfinite(hi)) || !(hi > lo)) return ORC_BAD_INTERVAL;
+    double cc = (lo + hi) / 2.0;
+    double ss = 2.0 / (hi - lo);
+    if (fp32) {
+        cc = (double)(float)cc;
+        ss = (double)(float)ss;
+    }
+    if (!isfinite(cc) || !isfinite(ss) || ss == 0.0) return ORC_BAD_INTERVAL;
+    *c = cc;
+    *s = ss;
+    return ORC_OK;
+}
+
+/*
+ * Power sums of Section II: S[k] = sum_i t_i^k (k = 0..2m) and
+ * T[k] = sum_i t_i^k y_i (k = 0..m), with t_i = x_i, or t_i = s*(x_i - c)
+ * when map != NULL (map = {c, s}).  One sequential pass, i = 0..n-1, powers
+ * by a running product; S[0] is the point count.
+ */
+void orc_powersums(const double* x, const double* y, int64_t n, int m,
+                   const double* map, double* S, double* T)
+{
+    for (int k = 0; k <= 2 * m; ++k) S[k] = 0.0;
+    for (int k = 0; k <= m; ++k) T[k] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double t = map ? map[1] * (x[i] - map[0]) : x[i];
+        double p = 1.0;
+        for (int k = 0; k <= 2 * m; ++k) {
+            if (k > 0) S[k] += p;
+            if (k <= m) T[k] += p * y[i];
+            p *= t;
+        }
+    }
+    S[0] = (double)n;
+}
+
+/* Gaussian elimination with partial pivoting of the (m+1)x(m+1) system
+ * M z = r, M row-major; M and r are overwritten.  Returns ORC_SINGULAR when
+ * a pivot is at or below (m+1)*eps64*max|M|. */
+static int orc_gauss_inplace(int m, double* M, double* r, double* z)
+{
+    const int N = m + 1;
+    double amax = 0.0;
+    for (int i = 0; i < N * N; ++i)
+        if (fabs(M[i]) > amax) amax = fabs(M[i]);
+    const double tol = (double)N * DBL_EPSILON * amax;
+    for (int k = 0; k < N; ++k) {
+        int p = k;
+        for (int i = k + 1; i < N; ++i)
+            if (fabs(M[i * N + k]) > fabs(M[p * N + k])) p = i;
+        if (!(fabs(M[p * N + k]) > tol)) return ORC_SINGULAR;
+        if (p != k) {
+            for (int j = 0; j < N; ++j) {
+                double tmp = M[k * N + j];
+                M[k * N + j] = M[p * N + j];
+                M[p * N + j] = tmp;
+            }
+            double tr = r[k];
+            r[k] = r[p];
+            r[p] = tr;
+        }
+        for (int i = k + 1; i < N; ++i) {
+            double f = M[i * N + k] / M[k * N + k];
+            for (int j = k; j < N; ++j) M[i * N + j] -= f * M[k * N + j];
+            r[i] -= f * r[k];
+        }
+    }
+    for (int i = N - 1; i >= 0; --i) {
+        double acc = r[i];
+        for (int j = i + 1; j < N; ++j) acc -= M[i * N + j] * z[j];
+        z[i] = acc / M[i * N + i];
+    }
+    for (int i = 0; i < N; ++i)
+        if (!isfinite(z[i])) return ORC_SINGULAR;
+    return ORC_OK;
+}
+
+/* Section II: A[j][k] = S[j+k], B[j] = T[j]; solve AX = B by Gaussian
+ * elimination.  Checks finiteness of the sums first. */
+int orc_solve(int m, const double* S, const double* T, double* X)
+{
+    if (m < 1 || m > ORC_MAX_M) return ORC_BAD_ARG;
+    const int N = m + 1;
+    for (int k = 0; k <= 2 * m; ++k)
+        if (!isfinite(S[k])) return ORC_NONFINITE;
+    for (int k = 0; k <= m; ++k)
+        if (!isfinite(T[k])) return ORC_NONFINITE;
+    double A[(ORC_MAX_M + 1) * (ORC_MAX_M + 1)];
+    double B[ORC_MAX_M + 1];
+    for (int j = 0; j < N; ++j) {
+        for (int k = 0; k < N; ++k) A[j * N + k] = S[j + k];
+        B[j] = T[j];
+    }
+    return orc_gauss_inplace(m, A, B, X);
+}
+
+/* Binomial coefficient C(k, j) as a double (exact for k <= 16). */
+static double orc_binom(int k, int j)
+{
+    double b = 1.0;
+    for (int i = 1; i <= j; ++i) b = b * (double)(k - j + i) / (double)i;
+    return b;
+}
+
+/* Coefficients of f(x) = sum_k Xt[k] (s(x - c))^k in the monomial basis of x:
+ * X[j] = sum_{k>=j} Xt[k] * C(k,j) * s^k * (-c)^(k-j). */
+void orc_unmap(int m, double c, double s, const double* Xt, double* X)
+{
+    for (int j = 0; j <= m; ++j) {
+        double acc = 0.0;
+        for (int k = j; k <= m; ++k)
+            acc += Xt[k] * orc_binom(k, j) * pow(s, (double)k) * pow(-c, (double)(k - j));
+        X[j] = acc;
+    }
+}
+
+/* Transpose of the un-map: g_t[k] = sum_{j<=k} C(k,j) s^k (-c)^(k-j) gX[j]. */
+static void orc_unmap_transpose(int m, double c, double s, const double* gX, double* gt)
+{
+    for (int k = 0; k <= m; ++k) {
+        double acc = 0.0;
+        for (int j = 0; j <= k; ++j)
+            acc += orc_binom(k, j) * pow(s, (double)k) * pow(-c, (double)(k - j)) * gX[j];
+        gt[k] = acc;
+    }
+}
+
+/*
+ * The whole fit: power sums, normal equations, Gaussian elimination, un-map.
+ * map = {c, s} or NULL.  Outputs (any may be NULL except X): X (x basis),
+ * Xt (t basis), S[2m+1], T[m+1].  Returns an ORC_* status; on failure X and
+ * Xt are NaN.
+ */
+int orc_fit(const double* x, const double* y, int64_t n, int m, const double* map,
+            double* X, double* Xt, double* S_out, double* T_out)
+{
+    double S[2 * ORC_MAX_M + 1], T[ORC_MAX_M + 1], Z[ORC_MAX_M + 1];
+    if (m < 1 || m > ORC_MAX_M) return ORC_BAD_ARG;
+    orc_powersums(x, y, n, m, map, S, T);
+    if (S_out) memcpy(S_out, S, sizeof(double) * (2 * m + 1));
+    if (T_out) memcpy(T_out, T, sizeof(double) * (m + 1));
+    int st = ORC_OK;
+    if (n < m + 1) st = ORC_N_TOO_SMALL;
+    else st = orc_solve(m, S, T, Z);
+    if (st != ORC_OK) {
+        for (int j = 0; j <= m; ++j) {
+            X[j] = NAN;
+            if (Xt) Xt[j] = NAN;
+        }
+        return st;
+    }
+    if (Xt) memcpy(Xt, Z, sizeof(double) * (m + 1));
+    if (map) orc_unmap(m, map[0], map[1], Z, X);
+    else memcpy(X, Z, sizeof(double) * (m + 1));
+    return ORC_OK;
+}
+
+/* Fitted values f(x_i) = sum_j X[j] x_i^j (Table V's y_f column). */
+void orc_eval(int m, const double* X, const double* x, int64_t n, double* f)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double acc = 0.0, p = 1.0;
+        for (int j = 0; j <= m; ++j) {
+            acc += X[j] * p;
+            p *= x[i];
+        }
+        f[i] = acc;
+    }
+}
+
+/* Sum of squared residuals, Section II's Pi for coefficients X (Table V). */
+double orc_sse(int m, const double* X, const double* x, const double* y, int64_t n)
+{
+    double sse = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double acc = 0.0, p = 1.0;
+        for (int j = 0; j <= m; ++j) {
+            acc += X[j] * p;
+            p *= x[i];
+        }
+        double e = y[i] - acc;
+        sse += e * e;
+    }
+    return sse;
+}
+
+/*
+ * Adjoint of orc_fit for a loss L(X) with gradient gX = dL/dX (x basis).
+ * The map constants are held fixed.  Steps:
+ *   g_t = M^T gX               (M: t-basis -> x-basis coefficient map);
+ *   lambda solves A lambda = g_t (A is symmetric, so A^T = A);
+ *   dy_i = lambda(t_i);
+ *   dt_i = lambda'(t_i) (y_i - f(t_i)) - lambda(t_i) f'(t_i), f = sum Xt_k t^k;
+ *   dx_i = s dt_i (dx_i = dt_i without a map).
+ * S holds the t-basis power sums S_0..S_2m, Xt the t-basis coefficients.
+ */
+int orc_backward(const double* x, const double* y, int64_t n, int m, const double* map,
+                 const double* S, const double* Xt, const double* gX,
+                 double* dx, double* dy)
+{
+    double gt[ORC_MAX_M + 1], A[(ORC_MAX_M + 1) * (ORC_MAX_M + 1)], lam[ORC_MAX_M + 1];
+    if (m < 1 || m > ORC_MAX_M) return ORC_BAD_ARG;
+    const int N = m + 1;
+    if (map) orc_unmap_transpose(m, map[0], map[1], gX, gt);
+    else memcpy(gt, gX, sizeof(double) * N);
+    for (int j = 0; j < N; ++j)
+        for (int k = 0; k < N; ++k) A[j * N + k] = S[j + k];
+    int st = orc_gauss_inplace(m, A, gt, lam);
+    if (st != ORC_OK) return st;
+    const double sc = map ? map[1] : 1.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double t = map ? map[1] * (x[i] - map[0]) : x[i];
+        double lv = 0.0, ld = 0.0, fv = 0.0, fd = 0.0;
+        double p = 1.0, pm1 = 0.0; /* t^j and t^(j-1) */
+        for (int j = 0; j <= m; ++j) {
+            lv += lam[j] * p;
+            fv += Xt[j] * p;
+            if (j > 0) {
+                ld += (double)j * lam[j] * pm1;
+                fd += (double)j * Xt[j] * pm1;
+            }
+            pm1 = p;
+            p *= t;
+        }
+        dy[i] = lv;
+        dx[i] = sc * (ld * (y[i] - fv) - lv * fd);
+    }
+    return ORC_OK;
+}
