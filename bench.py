@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the least-squares polynomial fit on one or more GPUs.
+
+Default workload (one step = one whole fit): a single series of n = 2^28
+FP32 points (2 GiB of x, y; larger than L2, so no flush is needed), x on
+[-1, 1], y a random cubic plus N(0, 0.01^2) noise.  A step streams the points
+once accumulating the degree-3 power sums (compensated FP32 accumulation,
+FP64 cross-block combine) and solves the normal equations for m = 3, 2 and 1
+from those sums (FP64 Gaussian elimination).  The metric is fitted points per
+second; the roofline is that of the streaming kernel (8 algorithmic bytes per
+point) against the measured HBM copy bandwidth.
+
+Other workloads (--workload) are measured the same way and documented with
+the library; the default line is the one the contract reports.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lsefit|reference]
+
+Under torchrun each rank fits its own independent series (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "fitted points/s (fwd)"
+UNIT = "points/s"
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["lsefit", "reference"], default="lsefit")
+    p.add_argument("--workload", default="single_large",
+                   choices=["single_large", "ragged_batch", "diff_batch", "single_fp64"])
+    p.add_argument("--n", type=int, default=1 << 28, help="points of the single_large series")
+    p.add_argument("--accum", default="comp", choices=["comp", "naive", "f64"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=10.0,
+                   help="target CPU time of the oracle baseline sample")
+    return p.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; no collective on the data path)
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self, gpus: int):
+        import torch
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if torch.cuda.is_available():
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+        elif torch.cuda.is_available():
+            torch.cuda.set_device(0)
+
+    def barrier(self):
+        if self.pg is not None:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        return self.reduce(v, "max")
+
+    def sum(self, v: float) -> float:
+        return self.reduce(v, "sum")
+
+    def reduce(self, v: float, op: str) -> float:
+        if self.pg is None:
+            return v
+        import torch
+        dev = torch.device("cuda", self.local) if torch.cuda.is_available() else torch.device("cpu")
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX if op == "max" else self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def source_digest() -> str:
+    """Hash of the CUDA sources (ties a recorded ncu traffic figure to the kernel it came from)."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1512_08017_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key: str):
+    """DRAM bytes per launch from profiles/traffic.json if taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kernel_key)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_digest") != source_digest():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, single thread, on a bounded sample
+# ---------------------------------------------------------------------------
+def cpu_baseline_single(x: np.ndarray, y: np.ndarray, m: int, target_s: float):
+    import oracle
+    n = x.size
+    sample = min(n, 1 << 24)
+    xs = x[:sample].astype(np.float64)
+    ys = y[:sample].astype(np.float64)
+    oracle.fit(xs[:1024], ys[:1024], m)  # build/load outside the timing
+    reps, t_total = 0, 0.0
+    while reps < 3 or t_total < target_s:
+        t0 = time.perf_counter()
+        out = oracle.fit(xs, ys, m)
+        t_total += time.perf_counter() - t0
+        reps += 1
+        if reps >= 1000:
+            break
+    assert out["status"] == "ok"
+    return {"value": sample * reps / t_total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {sample} points of the series, degree {m} fit "
+                      f"(FP64 sums + Gaussian elimination, sequential C), {reps} repetitions, "
+                      f"{t_total:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# single_large: one long FP32 series
+# ---------------------------------------------------------------------------
+def run_single_large(args, dist: Dist):
+    import torch
+    import synth
+    import paper_1512_08017_gb300 as L
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = args.n
+    m = 3
+    # each rank draws its own series (seed offset by rank)
+    hx = torch.empty(n, dtype=torch.float32).pin_memory()
+    hy = torch.empty(n, dtype=torch.float32).pin_memory()
+    d = synth.single_large(n=n, m=m, seed=synth.SEED_SINGLE_LARGE + dist.rank,
+                           out_x=hx.numpy(), out_y=hy.numpy())
+    x = hx.to(dev)
+    y = hy.to(dev)
+    stream = torch.cuda.current_stream()
+    sums = torch.empty(3 * m + 2, dtype=torch.float64, device=dev)
+    mp = torch.empty(2, dtype=torch.float64, device=dev)
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    Xs = {k: torch.empty(k + 1, dtype=torch.float64, device=dev) for k in (1, 2, 3)}
+    Xts = {k: torch.empty(k + 1, dtype=torch.float64, device=dev) for k in (1, 2, 3)}
+    sts = {k: torch.empty(1, dtype=torch.int32, device=dev) for k in (1, 2, 3)}
+
+    def step(ev_pair=None):
+        if ev_pair is not None:
+            ev_pair[0].record(stream)
+        L.powersums(x, y, m, args.accum, sums=sums, map_out=mp, status=st)
+        if ev_pair is not None:
+            ev_pair[1].record(stream)
+        for k in (3, 2, 1):
+            L.solve(sums, k, m, mp, X=Xs[k], Xt=Xts[k], status=sts[k])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # correctness of what is being timed (against the oracle) is the tests' job;
+    # here only the status is checked.
+    assert int(sts[3].item()) == L.OK
+
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for i in range(args.steps):
+        step(kev[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    kern_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
+    ms_max = dist.max(ms)
+    kern_ms_max = dist.max(kern_ms)
+
+    # end to end through the same C ABI with host buffers: H2D copy of the step's
+    # points from pinned memory, the fit, and the D2H read of the coefficients.
+    e2e = None
+    if not args.no_e2e:
+        hX = torch.empty(4, dtype=torch.float64).pin_memory()
+        e_steps = max(3, min(args.steps, 10))
+
+        def e2e_step():
+            x.copy_(hx, non_blocking=True)
+            y.copy_(hy, non_blocking=True)
+            step()
+            hX.copy_(Xs[3], non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e_steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = dist.max(e0.elapsed_time(e1))
+        e2e = {"value": dist.world * n * e_steps / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": 2 * n * 4, "d2h_bytes_per_step": 4 * 8,
+               "steps": e_steps, "ms_per_step": e_ms / e_steps}
+
+    peaks, peak_kind = measured_peaks()
+    algo_bytes = 8 * n
+    achieved = algo_bytes / (kern_ms_max / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": recorded_traffic("powersums_f32_comp_m3"),
+                "kernel": "ps_kernel_f32<3,F32,comp>", "kernel_ms": kern_ms_max,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6800 GB/s"}
+    cpu = None
+    if dist.rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_single(d["x"], d["y"], m, args.cpu_seconds)
+    value = dist.world * n * args.steps / (ms_max / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded; x ~ U[-1,1], y = random cubic + N(0, 0.01^2))",
+        "config": {"workload": "single series, n=2^28 FP32 points (2 GiB), degrees 3,2,1 from one pass",
+                   "n": n, "m": [3, 2, 1], "accum": args.accum, "solve": "fp64 GE, partial pivoting",
+                   "l2": "inputs (2 GiB) larger than L2; no flush", "parallelism": f"replicas x{dist.world}"},
+        "hbm_gbs": algo_bytes / (ms_max / args.steps / 1e3) / 1e9,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+        "gpu_launches": 4 * args.steps,
+    }
+    return line
+
+
+def run_reference(args, dist: Dist):
+    """The oracle timed on the host cores on the same workload and metric."""
+    if dist.rank != 0:
+        return None
+    import synth
+    import oracle
+    m = 3
+    sample = min(args.n, 1 << 24)
+    d = synth.single_large(n=sample, m=m, seed=synth.SEED_SINGLE_LARGE)
+    xs = d["x"].astype(np.float64)
+    ys = d["y"].astype(np.float64)
+    oracle.fit(xs[:1024], ys[:1024], m)
+    for _ in range(args.warmup):
+        oracle.fit(xs, ys, m)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        out = oracle.fit(xs, ys, m)
+        for k in (2, 1):
+            oracle.solve(out["S"][: 2 * k + 1], out["T"][: k + 1], k)
+    dt = time.perf_counter() - t0
+    value = sample * args.steps / dt
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "single series, n=2^28 FP32 points (2 GiB), degrees 3,2,1 from one pass",
+                       "sample_points_per_step": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {sample} points per step of the same series"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return 0
+        line = run_reference(args, type("D", (), {"rank": 0, "world": world})())
+        print(json.dumps(line))
+        return 0
+    import torch
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    dist = Dist(args.gpus)
+    try:
+        if args.workload == "single_large":
+            line = run_single_large(args, dist)
+        else:
+            import bench_workloads  # noqa: F401  (added with the batched paths)
+            line = bench_workloads.run(args, dist)
+        if dist.rank == 0 and line is not None:
+            print(json.dumps(line))
+    finally:
+        dist.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

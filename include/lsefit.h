@@ -1,0 +1,283 @@
+/*
+ * lsefit.h -- C ABI of the GB300 least-squares polynomial fit library.
+ *
+ * The library computes the matricized least-square-errors polynomial fit of
+ * Dasgupta, arXiv 1512.08017, Section II: for data pairs (x_i, y_i),
+ * i = 1..n, the polynomial f(x) = a_0 + a_1 x + ... + a_m x^m minimising
+ * Pi = sum_i [y_i - f(x_i)]^2 solves the normal equations
+ *     sum_i x_i^j y_i = sum_k a_k sum_i x_i^(j+k),   j = 0..m,
+ * written as A X = B with the Hankel matrix A[j][k] = S_{j+k},
+ * S_k = sum_i x_i^k (k = 0..2m), B[j] = T_j = sum_i x_i^j y_i (k = 0..m) and
+ * X = [a_0 .. a_m] (ascending order), solved by Gaussian elimination.
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named "device" must be device (or managed) memory of the
+ *    current CUDA device; "host" pointers are ordinary host memory.  The
+ *    point arrays x, y of lsefit_powersums may also be pinned, mapped host
+ *    memory (the kernel then streams over the host link).
+ *  - The caller owns every buffer.  The library allocates no device memory,
+ *    frees nothing and keeps no state between calls other than a per-device
+ *    cache of launch parameters.
+ *  - Every call is asynchronous on `stream` (NULL = the legacy default
+ *    stream).  The return value reports argument and launch errors only
+ *    (LSEFIT_OK on success).  Data-dependent outcomes (too few points, a
+ *    singular or non-finite system, a bad interval) are written per fit to a
+ *    device int32 status array with the same codes; coefficients of a
+ *    failed fit are NaN.
+ *  - Workspaces must be zero-filled once before their first use.  Every
+ *    call leaves its workspace zero-filled again where it needs zeros, so a
+ *    workspace can be reused by later calls on the same stream (and by CUDA
+ *    graph replays).  Two calls that run at the same time must not share a
+ *    workspace.
+ *  - Affine map.  When an interval [lo, hi] is given, every abscissa is
+ *    mapped to t = s (x - c) with c = (lo + hi) / 2, s = 2 / (hi - lo),
+ *    computed in FP64 and rounded once to the precision the points are
+ *    mapped in (FP32 for accum NAIVE/COMP, FP64 for accum F64).  The power
+ *    sums are those of t (the "mapped basis"), and the solver returns both
+ *    the mapped coefficients Xt (f = sum_k Xt_k t^k) and the coefficients X
+ *    of x obtained by expanding (s (x - c))^k in FP64.  Without an interval,
+ *    t = x.  The map is not in the paper; it keeps the Hankel system
+ *    well-conditioned.
+ *  - Degrees: 1 <= m <= LSEFIT_MAX_DEGREE.
+ */
+#ifndef LSEFIT_H
+#define LSEFIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (the same handle type). */
+typedef struct CUstream_st* lsefit_stream_t;
+
+#define LSEFIT_MAX_DEGREE 8
+#define LSEFIT_ABI_VERSION 1
+
+/* Return and status codes. */
+enum {
+    LSEFIT_OK = 0,
+    LSEFIT_ERR_INVALID_ARG = 1,   /* host: a null pointer, size or enum out of range */
+    LSEFIT_ERR_N_TOO_SMALL = 2,   /* per fit: n < m + 1 (the paper's n >= 2 only covers m = 1) */
+    LSEFIT_ERR_SINGULAR = 3,      /* per fit: a GE pivot <= (m+1) * eps64 * max|A| */
+    LSEFIT_ERR_NONFINITE = 4,     /* per fit: a power sum is Inf or NaN */
+    LSEFIT_ERR_BAD_INTERVAL = 5,  /* per fit: interval not finite or hi <= lo */
+    LSEFIT_ERR_WORKSPACE = 6,     /* host: workspace or plan buffer too small / misaligned */
+    LSEFIT_ERR_CUDA = 7,          /* host: a CUDA runtime call or launch failed */
+    LSEFIT_ERR_UNSUPPORTED = 8    /* host: dtype/accum combination not provided */
+};
+
+/* Storage type of x and y. */
+enum { LSEFIT_F64 = 0, LSEFIT_F32 = 1, LSEFIT_BF16 = 2 };
+
+/* Accumulation of the power sums.
+ *  NAIVE: per-point powers and sums in FP32 (per-thread FP32 sums, then an
+ *         exact-to-double-float reduction and an FP64 cross-block combine).
+ *  COMP:  per-point powers in FP32; per-thread sums kept as compensated
+ *         double-float (TwoSum) pairs, folded once per small register batch.
+ *  F64:   per-point map, powers and sums in FP64 (the only mode for F64 data). */
+enum { LSEFIT_ACCUM_NAIVE = 0, LSEFIT_ACCUM_COMP = 1, LSEFIT_ACCUM_F64 = 2 };
+
+/* Number of doubles in one set of sums for degree m: S_0..S_2m then T_0..T_m. */
+#define LSEFIT_SUMS_LEN(m) (3 * (m) + 2)
+
+/* Human-readable name of a return/status code (static string). */
+const char* lsefit_status_string(int code);
+
+/* LSEFIT_ABI_VERSION of the loaded library. */
+int lsefit_abi_version(void);
+
+/* ------------------------------------------------------------------------
+ * Single series
+ * ------------------------------------------------------------------------ */
+
+/* Bytes of workspace lsefit_powersums needs for any n on any device (an
+ * upper bound, computable without a GPU). */
+size_t lsefit_powersums_workspace_size(int m);
+
+/*
+ * lsefit_powersums -- the streaming pass that fills A and B (Section II:
+ * the entries of A are the sums S_k = sum_i x_i^k, k = 0..2m, and of B the
+ * sums T_k = sum_i x_i^k y_i, k = 0..m).
+ *
+ *  x, y       device (or mapped host) arrays of n points of `dtype`.  Any
+ *             element alignment is accepted; 16-byte-aligned arrays with the
+ *             same misalignment are streamed with 128-bit loads.
+ *  n          number of points, n >= 0 (n = 0 gives zero sums).
+ *  dtype      LSEFIT_F64 / LSEFIT_F32 / LSEFIT_BF16.
+ *  m          degree, 1..LSEFIT_MAX_DEGREE.
+ *  accum      LSEFIT_ACCUM_*; F64 data requires LSEFIT_ACCUM_F64.
+ *  interval   device double[2] = {lo, hi} or NULL (t = x).
+ *  sums       device double[3m+2], written: S_0..S_2m, T_0..T_m of t.
+ *             S_0 = n exactly.  NaN everywhere if the interval is bad.
+ *  map        device double[2] or NULL, written: {c, s} as used (the
+ *             identity {0, 1} without an interval; NaN if bad).
+ *  status     device int32[1] or NULL, written: LSEFIT_OK or
+ *             LSEFIT_ERR_BAD_INTERVAL.
+ *  workspace  device, >= lsefit_powersums_workspace_size(m) bytes,
+ *             256-byte aligned, zero-filled before first use.
+ * The result is bitwise reproducible for a given (n, dtype, m, accum,
+ * device): per-block partials are combined in FP64 in a fixed order.
+ */
+int lsefit_powersums(const void* x, const void* y, int64_t n, int dtype, int m, int accum,
+                     const double* interval, double* sums, double* map, int32_t* status,
+                     void* workspace, size_t workspace_bytes, lsefit_stream_t stream);
+
+/*
+ * lsefit_solve -- Gaussian elimination of AX = B (Section II builds A with
+ * A[j][k] = S_{j+k} and B[j] = T_j and solves the system by Gaussian
+ * elimination), in FP64 with partial pivoting (first row of largest
+ * magnitude), back-substitution, then the un-map of the coefficients.
+ *
+ *  sums    device double[count][3*m_sums+2], each row laid out as written by
+ *          lsefit_powersums for degree m_sums.
+ *  count   number of independent systems (>= 0).
+ *  m_sums  degree the sums were accumulated for (row layout).
+ *  m       degree to solve, 1 <= m <= m_sums: the sums of degree m_sums
+ *          contain those of every lower degree, so one pass serves several.
+ *  map     device double[count][2] {c, s} or NULL (identity).
+ *  X       device double[count][m+1]: coefficients of x, ascending.
+ *  Xt      device double[count][m+1] or NULL: coefficients of t.
+ *  status  device int32[count] or NULL: LSEFIT_OK, _N_TOO_SMALL (S_0 < m+1),
+ *          _NONFINITE, _SINGULAR or _BAD_INTERVAL (map not finite or s = 0).
+ */
+int lsefit_solve(const double* sums, int64_t count, int m_sums, int m, const double* map,
+                 double* X, double* Xt, int32_t* status, lsefit_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Batched ragged series (one persistent launch)
+ * ------------------------------------------------------------------------ */
+
+typedef struct lsefit_batch {
+    const void* x;            /* device, concatenated points of all series, dtype */
+    const void* y;            /* device, same layout as x */
+    const int64_t* offsets;   /* device int64[num_series+1]; series s is [offsets[s], offsets[s+1]) */
+    const int32_t* degree;    /* device int32[num_series], each in 1..m_max */
+    const double* interval;   /* device double[num_series][2] {lo, hi}, or NULL (t = x) */
+    int64_t num_series;
+    int32_t m_max;            /* row stride of X/Xt is m_max+1, of sums 3*m_max+2 */
+    int32_t dtype;            /* LSEFIT_F32 / LSEFIT_BF16 / LSEFIT_F64 */
+    int32_t accum;            /* LSEFIT_ACCUM_* */
+    int32_t reserved;
+} lsefit_batch;
+
+/* Tuning of the batched schedule (0 in a field = library default). */
+typedef struct lsefit_tuning {
+    int32_t warp_max_len;     /* series up to this length are reduced by one warp */
+    int32_t chunk_len;        /* longer series are cut into chunks of about this many points,
+                                 each reduced by one block; a series with one chunk is finished
+                                 by its block, others by the block that completes them last */
+    int32_t block_threads;    /* 128, 256 or 512 */
+    int32_t blocks_per_sm;    /* persistent blocks per SM (0 = occupancy maximum) */
+    int32_t reserved[4];
+} lsefit_tuning;
+
+/* Host-side schedule of one batch layout (built by lsefit_plan_build).  The two
+ * task arrays must be copied to device memory by the caller, who stores the
+ * device pointers in block_tasks / warp_tasks before calling lsefit_fit_batched. */
+typedef struct lsefit_plan {
+    int64_t num_series;
+    int64_t total_points;
+    int32_t n_block_tasks;    /* entries of block_tasks (4 int32 each) */
+    int32_t n_warp_tasks;     /* entries of warp_tasks (1 int32 each) */
+    int32_t n_split_series;   /* series cut into more than one chunk */
+    int32_t m_max;
+    lsefit_tuning tuning;     /* resolved values */
+    int32_t grid;             /* persistent grid size */
+    int32_t num_sms;
+    const int32_t* block_tasks;  /* device int32[n_block_tasks][4]: series, chunk, nchunks, first task */
+    const int32_t* warp_tasks;   /* device int32[n_warp_tasks]: series ids, longest first */
+} lsefit_plan;
+
+/*
+ * lsefit_plan_build -- split a batch layout into block tasks (series longer
+ * than tuning.warp_max_len, cut into chunks) and warp tasks (the shorter
+ * series), longest first.  Host only; no GPU needed.
+ *  offsets_host  host int64[num_series+1] (nondecreasing, offsets[0] = 0).
+ *  tuning        host, or NULL for defaults.
+ *  num_sms       SM count of the target device (> 0).
+ *  plan          host, written.
+ *  block_tasks_host / warp_tasks_host  host buffers of capacity
+ *                block_cap (entries of 4 int32) and warp_cap entries, written.
+ *                Pass NULL with zero capacity to query: plan->n_block_tasks
+ *                and plan->n_warp_tasks are still set, and the call returns
+ *                LSEFIT_ERR_WORKSPACE.
+ */
+int lsefit_plan_build(const int64_t* offsets_host, int64_t num_series, int m_max,
+                      const lsefit_tuning* tuning, int num_sms, lsefit_plan* plan,
+                      int32_t* block_tasks_host, int64_t block_cap,
+                      int32_t* warp_tasks_host, int64_t warp_cap);
+
+/* Bytes of workspace lsefit_fit_batched needs for `plan`. */
+size_t lsefit_batched_workspace_size(const lsefit_plan* plan);
+
+/*
+ * lsefit_fit_batched -- every step of the fit (map, power sums, Hankel
+ * system, Gaussian elimination, un-map; Section II) for each series of a
+ * ragged batch, in one persistent launch.  Series are reduced by a warp or,
+ * when longer, by one or more blocks (chunk partials combined in FP64 in a
+ * fixed order by the block that completes the series), and each series is
+ * solved right after its reduction.
+ *  batch     host descriptor (device arrays inside).
+ *  plan      host, from lsefit_plan_build for this layout, with device task arrays.
+ *  X         device double[num_series][m_max+1]; row s holds degree[s]+1
+ *            coefficients, the rest of the row is zero.
+ *  Xt        device, same shape, or NULL.
+ *  sums      device double[num_series][3*m_max+2] or NULL: S_0..S_2d, T_0..T_d
+ *            of degree d = degree[s] at the start of the row (needed by
+ *            lsefit_backward), rest zero.
+ *  map       device double[num_series][2] or NULL: {c, s} used per series.
+ *  status    device int32[num_series]: per-series status.
+ *  workspace device, >= lsefit_batched_workspace_size(plan), zero-filled before
+ *            first use.
+ */
+int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* plan, double* X,
+                       double* Xt, double* sums, double* map, int32_t* status,
+                       void* workspace, size_t workspace_bytes, lsefit_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Adjoint
+ * ------------------------------------------------------------------------ */
+
+/* Bytes of workspace lsefit_backward needs for `plan`. */
+size_t lsefit_backward_workspace_size(const lsefit_plan* plan);
+
+/*
+ * lsefit_backward -- gradient of a loss L(X) with respect to the points,
+ * given gX = dL/dX.  Not in the paper; derived from its normal equations
+ * (Section II) by the chain rule, with the map constants held fixed:
+ *   gt = M^T gX (M maps t-basis to x-basis coefficients);
+ *   lambda solves A lambda = gt (A symmetric), in FP64;
+ *   dL/dy_i = lambda(t_i);
+ *   dL/dx_i = s * [lambda'(t_i) (y_i - f(t_i)) - lambda(t_i) f'(t_i)],
+ *   with f(t) = sum_k Xt_k t^k; powers are recomputed, not stored.
+ * Two launches: the lambda solves (one series per thread), then a second
+ * pass over the points with the forward plan's tasks.
+ *  batch     as for lsefit_fit_batched (same layout and degrees).
+ *  plan      the forward's plan (same layout), device task arrays set.
+ *  sums      device double[num_series][3*m_max+2] from lsefit_fit_batched.
+ *  Xt        device double[num_series][m_max+1] from lsefit_fit_batched.
+ *  map       device double[num_series][2] from lsefit_fit_batched, or NULL
+ *            (identity map).
+ *  gX        device double[num_series][m_max+1]; entries beyond a series'
+ *            degree are ignored.
+ *  dx, dy    device arrays laid out like x, y: FP32 for F32/BF16 data, FP64
+ *            for F64 data.
+ *  status    device int32[num_series], written: LSEFIT_OK, or the reason the
+ *            adjoint system has no solution (_N_TOO_SMALL, _NONFINITE,
+ *            _SINGULAR, _BAD_INTERVAL, _INVALID_ARG for a bad degree); such
+ *            series get zero gradients.
+ *  workspace device, >= lsefit_backward_workspace_size(plan), 256-byte aligned,
+ *            zero-filled before first use.
+ */
+int lsefit_backward(const lsefit_batch* batch, const lsefit_plan* plan, const double* sums,
+                    const double* Xt, const double* map, const double* gX, void* dx, void* dy,
+                    int32_t* status, void* workspace, size_t workspace_bytes, lsefit_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSEFIT_H */

@@ -1,0 +1,393 @@
+// lsefit_backward.cu -- adjoint of the batched fit.
+//
+// The fit solves A Xt = B (Section II: A[j][k] = S_{j+k}, B[j] = T_j) on the
+// mapped abscissae t = s (x - c) and returns X = M Xt.  For a loss L(X) with
+// gX = dL/dX, the chain rule through the normal equations gives
+//   gt = M^T gX,  A lambda = gt  (A symmetric),
+//   dL/dT_j = lambda_j,  dL/dS_p = -sum_{j+k=p} lambda_j Xt_k,
+// and, through T_j = sum_i t_i^j y_i and S_p = sum_i t_i^p,
+//   dL/dy_i = lambda(t_i),
+//   dL/dt_i = lambda'(t_i) (y_i - f(t_i)) - lambda(t_i) f'(t_i),  f = sum_k Xt_k t^k,
+//   dL/dx_i = s dL/dt_i           (c and s held fixed).
+// Launch 1 solves for lambda, one series per thread (FP64, padded
+// elimination).  Launch 2 streams the points once more with the forward
+// plan's tasks, recomputing t and the polynomial values by Horner's rule
+// with derivative (packed FP32 pairs; FP64 for FP64 data).
+#include <cstring>
+
+#include "lsefit_device.cuh"
+#include "lsefit_host.h"
+
+namespace lsefit {
+
+constexpr int kBwBlock = 256;
+
+struct BwParams {
+    const void* x;
+    const void* y;
+    void* dx;
+    void* dy;
+    const int64_t* offsets;
+    const int32_t* degree;
+    int64_t num_series;
+    int m_max;
+    const double* Xt;       // [S][m_max+1]
+    const double* map;      // [S][2] or null
+    const double* lambda;   // [S][m_max+1] (workspace)
+    const int32_t* status;  // [S]
+    const int4* block_tasks;
+    int n_block_tasks;
+    const int32_t* warp_tasks;
+    int n_warp_tasks;
+    unsigned* counters;     // [0] block queue, [1] warp queue, [2] exited blocks
+};
+
+// ---------------------------------------------------------------------------
+// launch 1: lambda per series
+// ---------------------------------------------------------------------------
+template <int NMAX>
+__global__ void lambda_kernel(int64_t S, int m_max, const int32_t* degree, const double* sums,
+                              const double* map, const double* gX, double* lambda, int32_t* status) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int nc = m_max + 1;
+    const int m = degree[s];
+    double* lam = lambda + s * nc;
+    for (int j = 0; j < nc; ++j) lam[j] = 0.0;
+    if (m < 1 || m > m_max || m > NMAX) {
+        status[s] = LSEFIT_ERR_INVALID_ARG;
+        return;
+    }
+    const double* Srow = sums + s * (3 * m_max + 2);
+    double c = 0.0, sc = 1.0;
+    bool ok = true;
+    if (map) {
+        c = map[2 * s];
+        sc = map[2 * s + 1];
+        ok = isfinite(c) && isfinite(sc) && sc != 0.0;
+    }
+    int st = fit_precheck(m, Srow, Srow + 2 * m + 1, ok);
+    constexpr int N = NMAX + 1;
+    double gt[N], z[N];
+    if (st == LSEFIT_OK) {
+        // gt_k = sum_{j<=k} C(k,j) s^k (-c)^(k-j) gX_j
+        const double* g = gX + s * nc;
+        double binom[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) binom[j] = 0.0;
+        binom[0] = 1.0;
+        double sk = 1.0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            gt[k] = 0.0;
+            if (k <= m) {
+                if (k > 0) {
+#pragma unroll
+                    for (int j = N - 1; j >= 1; --j) binom[j] += binom[j - 1];
+                    sk *= sc;
+                }
+                double acc = 0.0, cp = 1.0;
+#pragma unroll
+                for (int j = N - 1; j >= 0; --j) {
+                    if (j <= k) {
+                        acc = fma(binom[j] * sk * cp, g[j], acc);
+                        cp *= -c;
+                    }
+                }
+                gt[k] = acc;
+            }
+        }
+        bool fin = true;
+#pragma unroll
+        for (int k = 0; k < N; ++k) fin = fin && isfinite(gt[k]);
+        st = fin ? hankel_ge<NMAX>(m, Srow, gt, z) : LSEFIT_ERR_NONFINITE;
+    }
+    if (st == LSEFIT_OK) {
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+            if (j <= m) lam[j] = z[j];
+    }
+    status[s] = st;
+}
+
+// ---------------------------------------------------------------------------
+// launch 2: gradients per point
+// ---------------------------------------------------------------------------
+template <int DT>
+struct OutT {
+    typedef float T;
+};
+template <>
+struct OutT<LSEFIT_F64> {
+    typedef double T;
+};
+
+// Horner's rule with derivative for (lambda, f) on a pair of points.
+template <int M>
+__device__ __forceinline__ void grad_pair(const u64* lam, const u64* xt, u64 t, u64 y, u64 s2, u64& dxv,
+                                          u64& dyv) {
+    u64 lv = lam[M], ld = 0ull, fv = xt[M], fd = 0ull;
+#pragma unroll
+    for (int j = M - 1; j >= 0; --j) {
+        ld = fma2(ld, t, lv);
+        lv = fma2(lv, t, lam[j]);
+        fd = fma2(fd, t, fv);
+        fv = fma2(fv, t, xt[j]);
+    }
+    const u64 r = sub2(y, fv);
+    // s * (ld * r - lv * fd)
+    const u64 a = mul2(lv, fd);
+    const u64 g = fma2(ld, r, a ^ 0x8000000080000000ull);  // ld*r + (-(lv*fd))
+    dxv = mul2(g, s2);
+    dyv = lv;
+}
+
+template <int M, int DT>
+__device__ __forceinline__ void grad_range_f32(const BwParams& p, int64_t b, int64_t e, int64_t rank,
+                                               int64_t nthreads, const double* lam64, const double* xt64,
+                                               double c, double sc) {
+    constexpr int ES = Elem<DT>::kSize, PV = Elem<DT>::kPerVec;
+    u64 lam[M + 1], xt[M + 1];
+#pragma unroll
+    for (int j = 0; j <= M; ++j) {
+        const float l = (float)lam64[j], f = (float)xt64[j];
+        lam[j] = pk2(l, l);
+        xt[j] = pk2(f, f);
+    }
+    const float cf = (float)c, sf = (float)sc;
+    const u64 c2 = pk2(cf, cf), s2 = pk2(sf, sf);
+    float* dx = static_cast<float*>(p.dx);
+    float* dy = static_cast<float*>(p.dy);
+    // vector path needs x, y, dx, dy at the same offset within their 16-byte groups
+    // (outputs are FP32: for BF16 data the output vectors are 2x wider; scalar path then)
+    int64_t head, nvec;
+    split_range<DT>(p.x, p.y, b, e, head, nvec);
+    const uintptr_t xa = reinterpret_cast<uintptr_t>(p.x) + (uintptr_t)b * ES;
+    const uintptr_t da = reinterpret_cast<uintptr_t>(dx) + (uintptr_t)b * 4;
+    const uintptr_t ea = reinterpret_cast<uintptr_t>(dy) + (uintptr_t)b * 4;
+    if (DT != LSEFIT_F32 || (xa & 15) != (da & 15) || (da & 15) != (ea & 15)) {
+        head = e - b;
+        nvec = 0;
+    }
+    const uint4* xv = reinterpret_cast<const uint4*>(static_cast<const char*>(p.x) + (b + head) * ES);
+    const uint4* yv = reinterpret_cast<const uint4*>(static_cast<const char*>(p.y) + (b + head) * ES);
+    float4* dxv = reinterpret_cast<float4*>(dx + b + head);
+    float4* dyv = reinterpret_cast<float4*>(dy + b + head);
+    for (int64_t v = rank; v < nvec; v += nthreads) {
+        const uint4 xr = ld_stream16(xv + v), yr = ld_stream16(yv + v);
+        u64 ta = mul2(sub2(pk2(__uint_as_float(xr.x), __uint_as_float(xr.y)), c2), s2);
+        u64 tb = mul2(sub2(pk2(__uint_as_float(xr.z), __uint_as_float(xr.w)), c2), s2);
+        u64 ya = pk2(__uint_as_float(yr.x), __uint_as_float(yr.y));
+        u64 yb = pk2(__uint_as_float(yr.z), __uint_as_float(yr.w));
+        u64 gxa, gya, gxb, gyb;
+        grad_pair<M>(lam, xt, ta, ya, s2, gxa, gya);
+        grad_pair<M>(lam, xt, tb, yb, s2, gxb, gyb);
+        float4 ox, oy;
+        up2(gxa, ox.x, ox.y);
+        up2(gxb, ox.z, ox.w);
+        up2(gya, oy.x, oy.y);
+        up2(gyb, oy.z, oy.w);
+        __stcs(dxv + v, ox);
+        __stcs(dyv + v, oy);
+    }
+    const int64_t tail0 = b + head + nvec * PV;
+    const int64_t nscalar = head + (e - tail0);
+    for (int64_t q = rank; q < nscalar; q += nthreads) {
+        const int64_t i = q < head ? b + q : tail0 + (q - head);
+        const float xs = Elem<DT>::ld(p.x, i), ys = Elem<DT>::ld(p.y, i);
+        const float ts = __fmul_rn(__fsub_rn(xs, cf), sf);
+        u64 gx, gy;
+        grad_pair<M>(lam, xt, pk2(ts, 0.0f), pk2(ys, 0.0f), s2, gx, gy);
+        float a0, a1, b0, b1;
+        up2(gx, a0, a1);
+        up2(gy, b0, b1);
+        dx[i] = a0;
+        dy[i] = b0;
+    }
+}
+
+template <int M>
+__device__ __forceinline__ void grad_range_f64(const BwParams& p, int64_t b, int64_t e, int64_t rank,
+                                               int64_t nthreads, const double* lam, const double* xt,
+                                               double c, double sc) {
+    double* dx = static_cast<double*>(p.dx);
+    double* dy = static_cast<double*>(p.dy);
+    for (int64_t i = b + rank; i < e; i += nthreads) {
+        const double t = sc * (Elem<LSEFIT_F64>::ld64(p.x, i) - c);
+        double lv = lam[M], ld = 0.0, fv = xt[M], fd = 0.0;
+#pragma unroll
+        for (int j = M - 1; j >= 0; --j) {
+            ld = fma(ld, t, lv);
+            lv = fma(lv, t, lam[j]);
+            fd = fma(fd, t, fv);
+            fv = fma(fv, t, xt[j]);
+        }
+        const double r = Elem<LSEFIT_F64>::ld64(p.y, i) - fv;
+        dx[i] = sc * (ld * r - lv * fd);
+        dy[i] = lv;
+    }
+}
+
+// Zero gradients of a series that has no valid adjoint.
+template <int DT>
+__device__ __forceinline__ void zero_range(const BwParams& p, int64_t b, int64_t e, int64_t rank, int64_t nthreads) {
+    typedef typename OutT<DT>::T T;
+    T* dx = static_cast<T*>(p.dx);
+    T* dy = static_cast<T*>(p.dy);
+    for (int64_t i = b + rank; i < e; i += nthreads) {
+        dx[i] = (T)0;
+        dy[i] = (T)0;
+    }
+}
+
+template <int DT, int M>
+__device__ __forceinline__ void grad_task(const BwParams& p, int64_t s, int64_t b, int64_t e, int64_t rank,
+                                          int64_t nthreads) {
+    const int nc = p.m_max + 1;
+    const double* lam = p.lambda + s * nc;
+    const double* xt = p.Xt + s * nc;
+    const double c = p.map ? p.map[2 * s] : 0.0;
+    const double sc = p.map ? p.map[2 * s + 1] : 1.0;
+    if constexpr (DT == LSEFIT_F64) {
+        double l[M + 1], f[M + 1];
+#pragma unroll
+        for (int j = 0; j <= M; ++j) {
+            l[j] = lam[j];
+            f[j] = xt[j];
+        }
+        grad_range_f64<M>(p, b, e, rank, nthreads, l, f, c, sc);
+    } else {
+        double l[M + 1], f[M + 1];
+#pragma unroll
+        for (int j = 0; j <= M; ++j) {
+            l[j] = lam[j];
+            f[j] = xt[j];
+        }
+        grad_range_f32<M, DT>(p, b, e, rank, nthreads, l, f, c, sc);
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ void grad_dispatch(const BwParams& p, int64_t s, int64_t b, int64_t e, int64_t rank,
+                                              int64_t nthreads) {
+    const int m = p.degree[s];
+    if (p.status[s] != LSEFIT_OK || m < 1 || m > p.m_max) {
+        zero_range<DT>(p, b, e, rank, nthreads);
+        return;
+    }
+    switch (m) {
+        case 1: grad_task<DT, 1>(p, s, b, e, rank, nthreads); break;
+        case 2: grad_task<DT, 2>(p, s, b, e, rank, nthreads); break;
+        case 3: grad_task<DT, 3>(p, s, b, e, rank, nthreads); break;
+        case 4: grad_task<DT, 4>(p, s, b, e, rank, nthreads); break;
+        case 5: grad_task<DT, 5>(p, s, b, e, rank, nthreads); break;
+        case 6: grad_task<DT, 6>(p, s, b, e, rank, nthreads); break;
+        case 7: grad_task<DT, 7>(p, s, b, e, rank, nthreads); break;
+        default: grad_task<DT, 8>(p, s, b, e, rank, nthreads); break;
+    }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kBwBlock) grad_kernel(BwParams p) {
+    __shared__ int s_task;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (;;) {
+        if (tid == 0) s_task = (int)atomicAdd(&p.counters[0], 1u);
+        __syncthreads();
+        const int t = s_task;
+        __syncthreads();
+        if (t >= p.n_block_tasks) break;
+        const int4 task = p.block_tasks[t];
+        const int64_t s = task.x;
+        const int64_t b0 = p.offsets[s], e0 = p.offsets[s + 1];
+        const int64_t per = ((e0 - b0 + task.z - 1) / task.z + 7) / 8 * 8;
+        const int64_t b = min(b0 + (int64_t)task.y * per, e0);
+        const int64_t e = min(b + per, e0);
+        grad_dispatch<DT>(p, s, b, e, tid, kBwBlock);
+    }
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = (int)atomicAdd(&p.counters[1], 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= p.n_warp_tasks) break;
+        const int64_t s = p.warp_tasks[t];
+        grad_dispatch<DT>(p, s, p.offsets[s], p.offsets[s + 1], lane, 32);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&p.counters[2], 1u) == gridDim.x - 1) {
+            p.counters[0] = 0u;
+            p.counters[1] = 0u;
+            p.counters[2] = 0u;
+        }
+    }
+}
+
+}  // namespace lsefit
+
+using namespace lsefit;
+
+extern "C" size_t lsefit_backward_workspace_size(const lsefit_plan* plan) {
+    if (plan == nullptr || plan->m_max < 1) return 0;
+    return kAlign + align_up((size_t)plan->num_series * (plan->m_max + 1) * sizeof(double), kAlign);
+}
+
+extern "C" int lsefit_backward(const lsefit_batch* batch, const lsefit_plan* plan, const double* sums,
+                               const double* Xt, const double* map, const double* gX, void* dx, void* dy,
+                               int32_t* status, void* workspace, size_t workspace_bytes,
+                               lsefit_stream_t stream) {
+    if (batch == nullptr || plan == nullptr || status == nullptr) return LSEFIT_ERR_INVALID_ARG;
+    const lsefit_batch& b = *batch;
+    if (b.num_series != plan->num_series || b.m_max != plan->m_max || b.m_max < 1 ||
+        b.m_max > LSEFIT_MAX_DEGREE)
+        return LSEFIT_ERR_INVALID_ARG;
+    if (b.dtype < LSEFIT_F64 || b.dtype > LSEFIT_BF16) return LSEFIT_ERR_INVALID_ARG;
+    if (b.num_series == 0) return LSEFIT_OK;
+    if (sums == nullptr || Xt == nullptr || gX == nullptr || b.offsets == nullptr || b.degree == nullptr)
+        return LSEFIT_ERR_INVALID_ARG;
+    if (plan->total_points > 0 && (b.x == nullptr || b.y == nullptr || dx == nullptr || dy == nullptr))
+        return LSEFIT_ERR_INVALID_ARG;
+    if (workspace == nullptr || !aligned(workspace, kAlign) ||
+        workspace_bytes < lsefit_backward_workspace_size(plan))
+        return LSEFIT_ERR_WORKSPACE;
+    char* ws = static_cast<char*>(workspace);
+    double* lambda = reinterpret_cast<double*>(ws + kAlign);
+    const int threads = 64;
+    const int64_t blocks = (b.num_series + threads - 1) / threads;
+    auto lk = b.m_max <= 3 ? lambda_kernel<3> : b.m_max <= 5 ? lambda_kernel<5> : lambda_kernel<8>;
+    lk<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(b.num_series, b.m_max, b.degree, sums, map, gX,
+                                                              lambda, status);
+    if (cudaGetLastError() != cudaSuccess) return LSEFIT_ERR_CUDA;
+
+    BwParams p;
+    p.x = b.x;
+    p.y = b.y;
+    p.dx = dx;
+    p.dy = dy;
+    p.offsets = b.offsets;
+    p.degree = b.degree;
+    p.num_series = b.num_series;
+    p.m_max = b.m_max;
+    p.Xt = Xt;
+    p.map = map;
+    p.lambda = lambda;
+    p.status = status;
+    p.block_tasks = reinterpret_cast<const int4*>(plan->block_tasks);
+    p.n_block_tasks = plan->n_block_tasks;
+    p.warp_tasks = plan->warp_tasks;
+    p.n_warp_tasks = plan->n_warp_tasks;
+    p.counters = reinterpret_cast<unsigned*>(ws);
+    auto gk = b.dtype == LSEFIT_F64 ? grad_kernel<LSEFIT_F64>
+              : b.dtype == LSEFIT_F32 ? grad_kernel<LSEFIT_F32> : grad_kernel<LSEFIT_BF16>;
+    int dev = 0;
+    const int sms = current_sm_count(&dev);
+    if (sms <= 0) return LSEFIT_ERR_CUDA;
+    const int occ = occupancy_blocks(reinterpret_cast<const void*>(gk), kBwBlock, 0);
+    int64_t grid = (int64_t)sms * occ;
+    const int64_t useful = (int64_t)plan->n_block_tasks + (plan->n_warp_tasks + 7) / 8;
+    if (useful < grid) grid = useful;
+    if (grid < 1) grid = 1;
+    gk<<<(unsigned)grid, kBwBlock, 0, (cudaStream_t)stream>>>(p);
+    return cudaGetLastError() == cudaSuccess ? LSEFIT_OK : LSEFIT_ERR_CUDA;
+}

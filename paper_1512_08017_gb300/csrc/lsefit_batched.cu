@@ -1,0 +1,180 @@
+// lsefit_batched.cu -- host side of the batched fit: the schedule (plan),
+// workspace sizing and the launch of the persistent kernel of
+// lsefit_batched.cuh.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "lsefit_batched.cuh"
+#include "lsefit_host.h"
+
+namespace lsefit {
+
+static batched_kernel_t pick_batched(int dtype, int accum, int nmax) {
+    if (dtype == LSEFIT_F64) return batched_f64_f64(nmax);
+    if (dtype == LSEFIT_F32) {
+        if (accum == LSEFIT_ACCUM_NAIVE) return batched_f32_naive(nmax);
+        if (accum == LSEFIT_ACCUM_COMP) return batched_f32_comp(nmax);
+        return batched_f32_f64(nmax);
+    }
+    if (accum == LSEFIT_ACCUM_NAIVE) return batched_bf16_naive(nmax);
+    if (accum == LSEFIT_ACCUM_COMP) return batched_bf16_comp(nmax);
+    return batched_bf16_f64(nmax);
+}
+
+static void resolve_tuning(const lsefit_tuning* in, lsefit_tuning* out) {
+    lsefit_tuning t;
+    std::memset(&t, 0, sizeof(t));
+    if (in) t = *in;
+    if (t.warp_max_len <= 0) t.warp_max_len = kDefaultWarpMaxLen;
+    if (t.chunk_len <= 0) t.chunk_len = kDefaultChunkLen;
+    if (t.chunk_len < 1024) t.chunk_len = 1024;
+    t.block_threads = kBBlock;
+    if (t.blocks_per_sm < 0) t.blocks_per_sm = 0;
+    *out = t;
+}
+
+}  // namespace lsefit
+
+using namespace lsefit;
+
+extern "C" int lsefit_plan_build(const int64_t* offsets, int64_t num_series, int m_max,
+                                 const lsefit_tuning* tuning, int num_sms, lsefit_plan* plan,
+                                 int32_t* block_tasks, int64_t block_cap, int32_t* warp_tasks,
+                                 int64_t warp_cap) {
+    if (plan == nullptr || offsets == nullptr || num_series < 0 || num_series >= (int64_t(1) << 31) ||
+        m_max < 1 || m_max > LSEFIT_MAX_DEGREE || num_sms <= 0)
+        return LSEFIT_ERR_INVALID_ARG;
+    if (offsets[0] != 0) return LSEFIT_ERR_INVALID_ARG;
+    for (int64_t s = 0; s < num_series; ++s)
+        if (offsets[s + 1] < offsets[s]) return LSEFIT_ERR_INVALID_ARG;
+    std::memset(plan, 0, sizeof(*plan));
+    resolve_tuning(tuning, &plan->tuning);
+    const int64_t wmax = plan->tuning.warp_max_len, ch = plan->tuning.chunk_len;
+    std::vector<int32_t> longs, shorts;
+    int64_t nbt = 0;
+    int nsplit = 0;
+    for (int64_t s = 0; s < num_series; ++s) {
+        const int64_t len = offsets[s + 1] - offsets[s];
+        if (len > wmax) {
+            longs.push_back((int32_t)s);
+            const int64_t nch = (len + ch - 1) / ch;
+            nbt += nch;
+            if (nch > 1) ++nsplit;
+        } else {
+            shorts.push_back((int32_t)s);
+        }
+    }
+    if (nbt >= (int64_t(1) << 31)) return LSEFIT_ERR_INVALID_ARG;
+    plan->num_series = num_series;
+    plan->total_points = offsets[num_series];
+    plan->n_block_tasks = (int32_t)nbt;
+    plan->n_warp_tasks = (int32_t)shorts.size();
+    plan->n_split_series = nsplit;
+    plan->m_max = m_max;
+    plan->num_sms = num_sms;
+    plan->grid = 0;
+    if (block_cap < nbt || warp_cap < (int64_t)shorts.size() || (nbt > 0 && block_tasks == nullptr) ||
+        (!shorts.empty() && warp_tasks == nullptr))
+        return LSEFIT_ERR_WORKSPACE;
+    auto len_of = [&](int32_t s) { return offsets[s + 1] - offsets[s]; };
+    auto longer = [&](int32_t a, int32_t b) { return len_of(a) > len_of(b); };
+    std::stable_sort(longs.begin(), longs.end(), longer);
+    std::stable_sort(shorts.begin(), shorts.end(), longer);
+    int64_t t = 0;
+    for (int32_t s : longs) {
+        const int64_t nch = (len_of(s) + ch - 1) / ch;
+        const int64_t first = t;
+        for (int64_t c = 0; c < nch; ++c, ++t) {
+            block_tasks[4 * t + 0] = s;
+            block_tasks[4 * t + 1] = (int32_t)c;
+            block_tasks[4 * t + 2] = (int32_t)nch;
+            block_tasks[4 * t + 3] = (int32_t)first;
+        }
+    }
+    std::copy(shorts.begin(), shorts.end(), warp_tasks);
+    return LSEFIT_OK;
+}
+
+extern "C" size_t lsefit_batched_workspace_size(const lsefit_plan* plan) {
+    if (plan == nullptr) return 0;
+    const size_t nbt = plan->n_block_tasks > 0 ? (size_t)plan->n_block_tasks : 0;
+    return kAlign + align_up(nbt * sizeof(unsigned), kAlign) +
+           align_up(nbt * (size_t)(3 * plan->m_max + 1) * sizeof(double), kAlign);
+}
+
+extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* plan, double* X,
+                                  double* Xt, double* sums, double* map, int32_t* status,
+                                  void* workspace, size_t workspace_bytes, lsefit_stream_t stream) {
+    if (batch == nullptr || plan == nullptr || X == nullptr || status == nullptr) return LSEFIT_ERR_INVALID_ARG;
+    const lsefit_batch& b = *batch;
+    if (b.num_series != plan->num_series || b.m_max != plan->m_max || b.m_max < 1 ||
+        b.m_max > LSEFIT_MAX_DEGREE)
+        return LSEFIT_ERR_INVALID_ARG;
+    if (b.dtype < LSEFIT_F64 || b.dtype > LSEFIT_BF16 || b.accum < LSEFIT_ACCUM_NAIVE ||
+        b.accum > LSEFIT_ACCUM_F64)
+        return LSEFIT_ERR_INVALID_ARG;
+    if (b.dtype == LSEFIT_F64 && b.accum != LSEFIT_ACCUM_F64) return LSEFIT_ERR_UNSUPPORTED;
+    if (b.num_series == 0) return LSEFIT_OK;
+    if (b.offsets == nullptr || b.degree == nullptr) return LSEFIT_ERR_INVALID_ARG;
+    if (plan->total_points > 0 && (b.x == nullptr || b.y == nullptr)) return LSEFIT_ERR_INVALID_ARG;
+    if ((plan->n_block_tasks > 0 && plan->block_tasks == nullptr) ||
+        (plan->n_warp_tasks > 0 && plan->warp_tasks == nullptr))
+        return LSEFIT_ERR_INVALID_ARG;
+    if (workspace == nullptr || !aligned(workspace, kAlign) ||
+        workspace_bytes < lsefit_batched_workspace_size(plan))
+        return LSEFIT_ERR_WORKSPACE;
+
+    BParams p;
+    p.x = b.x;
+    p.y = b.y;
+    p.offsets = b.offsets;
+    p.degree = b.degree;
+    p.interval = b.interval;
+    p.num_series = b.num_series;
+    p.m_max = b.m_max;
+    p.block_tasks = reinterpret_cast<const int4*>(plan->block_tasks);
+    p.n_block_tasks = plan->n_block_tasks;
+    p.warp_tasks = plan->warp_tasks;
+    p.n_warp_tasks = plan->n_warp_tasks;
+    p.X = X;
+    p.Xt = Xt;
+    p.sums = sums;
+    p.map = map;
+    p.status = status;
+    char* ws = static_cast<char*>(workspace);
+    p.counters = reinterpret_cast<unsigned*>(ws);
+    p.tickets = reinterpret_cast<unsigned*>(ws + kAlign);
+    p.partials = reinterpret_cast<double*>(
+        ws + kAlign + align_up((size_t)plan->n_block_tasks * sizeof(unsigned), kAlign));
+
+    const int nmax = b.m_max <= 5 ? 5 : 8;
+    batched_kernel_t k = pick_batched(b.dtype, b.accum, nmax);
+    const size_t smem = batched_smem_bytes(nmax);
+    static std::mutex mu;
+    static std::vector<std::pair<int, const void*>> configured;
+    int dev = 0;
+    const int sms = current_sm_count(&dev);
+    if (sms <= 0) return LSEFIT_ERR_CUDA;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        const std::pair<int, const void*> key(dev, reinterpret_cast<const void*>(k));
+        if (std::find(configured.begin(), configured.end(), key) == configured.end()) {
+            if (cudaFuncSetAttribute(reinterpret_cast<const void*>(k),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+                return LSEFIT_ERR_CUDA;
+            configured.push_back(key);
+        }
+    }
+    int bps = plan->tuning.blocks_per_sm;
+    const int occ = occupancy_blocks(reinterpret_cast<const void*>(k), kBBlock, smem);
+    if (bps <= 0 || bps > occ) bps = occ;
+    int64_t grid = (int64_t)sms * bps;
+    const int64_t useful = (int64_t)plan->n_block_tasks + (plan->n_warp_tasks + kBWarps - 1) / kBWarps;
+    if (useful < grid) grid = useful;
+    if (grid < 1) grid = 1;
+    k<<<(unsigned)grid, kBBlock, smem, (cudaStream_t)stream>>>(p);
+    return cudaGetLastError() == cudaSuccess ? LSEFIT_OK : LSEFIT_ERR_CUDA;
+}

@@ -1,0 +1,670 @@
+// lsefit_device.cuh -- device building blocks of the least-squares polynomial fit.
+//
+// The fit (Dasgupta, arXiv 1512.08017, Section II) needs, for every point,
+// the powers t^k (k <= 2m) added into S_k and t^k y added into T_k, then
+// the Hankel system A[j][k] = S_{j+k}, B[j] = T_j solved by Gaussian
+// elimination.  This header holds:
+//   * packed FP32 pair arithmetic (Blackwell add/sub/mul/fma .f32x2): two
+//     points per instruction in the per-point loop;
+//   * TwoSum / double-float helpers for compensated accumulation;
+//   * point loaders for F32 / BF16 / F64 storage;
+//   * the per-thread accumulator (naive FP32, compensated, FP64);
+//   * the block reduction of accumulators (double-float, fixed order);
+//   * the FP64 Hankel solve with partial pivoting and the un-map.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lsefit.h"
+
+namespace lsefit {
+
+typedef unsigned long long u64;
+
+// ---------------------------------------------------------------------------
+// Packed FP32 pairs.  Each lane of a pair is an independent IEEE RN operation.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ u64 pk2(float lo, float hi) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void up2(u64 v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// Error-free transformations (Knuth's TwoSum, Dekker's Fast2Sum) and a
+// double-float value hi + lo.  Intrinsics keep every step a single rounding.
+// ---------------------------------------------------------------------------
+struct dflt {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ dflt df_add(dflt a, dflt b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    dflt r;
+    r.hi = __fadd_rn(s, e);
+    r.lo = __fsub_rn(e, __fsub_rn(r.hi, s));
+    return r;
+}
+
+__device__ __forceinline__ dflt df_shfl_xor(dflt v, int mask) {
+    dflt r;
+    r.hi = __shfl_xor_sync(0xffffffffu, v.hi, mask);
+    r.lo = __shfl_xor_sync(0xffffffffu, v.lo, mask);
+    return r;
+}
+
+__device__ __forceinline__ double df_to_double(dflt v) { return (double)v.hi + (double)v.lo; }
+
+// TwoSum on both lanes of a pair: (hi, lo) += b with the rounding error of
+// the high sum carried into lo.
+__device__ __forceinline__ void fold2(u64& hi, u64& lo, u64 b) {
+    u64 s = add2(hi, b);
+    u64 bb = sub2(s, hi);
+    u64 e = add2(sub2(hi, sub2(s, bb)), sub2(b, bb));
+    lo = add2(lo, e);
+    hi = s;
+}
+
+// ---------------------------------------------------------------------------
+// BF16 helpers (bit operations; a bfloat16 is the top half of an FP32).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+template <int DT>
+struct Elem;
+template <>
+struct Elem<LSEFIT_F32> {
+    typedef float T;
+    static constexpr int kSize = 4;
+    static constexpr int kPerVec = 4;  // points per 16-byte vector
+    __device__ static __forceinline__ float ld(const void* p, int64_t i) {
+        return __ldg(reinterpret_cast<const float*>(p) + i);
+    }
+    __device__ static __forceinline__ double ld64(const void* p, int64_t i) { return (double)ld(p, i); }
+};
+template <>
+struct Elem<LSEFIT_BF16> {
+    typedef uint16_t T;
+    static constexpr int kSize = 2;
+    static constexpr int kPerVec = 8;
+    __device__ static __forceinline__ float ld(const void* p, int64_t i) {
+        uint16_t b = __ldg(reinterpret_cast<const unsigned short*>(p) + i);
+        return __uint_as_float(((uint32_t)b) << 16);
+    }
+    __device__ static __forceinline__ double ld64(const void* p, int64_t i) { return (double)ld(p, i); }
+};
+template <>
+struct Elem<LSEFIT_F64> {
+    typedef double T;
+    static constexpr int kSize = 8;
+    static constexpr int kPerVec = 2;
+    __device__ static __forceinline__ double ld64(const void* p, int64_t i) {
+        return __ldg(reinterpret_cast<const double*>(p) + i);
+    }
+};
+
+// 16-byte vector load that is not kept in L1 (streamed once).
+__device__ __forceinline__ uint4 ld_stream16(const void* p) {
+    uint4 r;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p));
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Map constants.  c = (lo + hi) / 2, s = 2 / (hi - lo) in FP64, rounded once
+// to FP32 when the points are mapped in FP32.  Identity without an interval.
+// Returns false for an interval that is not finite or has hi <= lo.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool map_constants(const double* interval, bool fp32, double& c, double& s) {
+    if (interval == nullptr) {
+        c = 0.0;
+        s = 1.0;
+        return true;
+    }
+    const double lo = interval[0], hi = interval[1];
+    if (!(isfinite(lo) && isfinite(hi)) || !(hi > lo)) {
+        c = 0.0;
+        s = 1.0;
+        return false;
+    }
+    double cc = (lo + hi) * 0.5;
+    double ss = 2.0 / (hi - lo);
+    if (fp32) {
+        cc = (double)__double2float_rn(cc);
+        ss = (double)__double2float_rn(ss);
+    }
+    if (!isfinite(cc) || !isfinite(ss) || ss == 0.0) {
+        c = 0.0;
+        s = 1.0;
+        return false;
+    }
+    c = cc;
+    s = ss;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Per-thread accumulators for degree M.  Accumulator a: a < 2M holds S_{a+1},
+// a >= 2M holds T_{a-2M}.  (S_0 is the exact point count, never summed.)
+// ---------------------------------------------------------------------------
+template <int M>
+struct Nacc {
+    static constexpr int value = 3 * M + 1;
+};
+
+// FP32 pair accumulator: each u64 carries two independent lane sums.
+// COMP adds a (hi, lo) TwoSum pair per accumulator, fed once per batch.
+template <int M, bool COMP>
+struct AccF32 {
+    static constexpr int N = 3 * M + 1;
+    u64 acc[N];
+    u64 hi[COMP ? N : 1];
+    u64 lo[COMP ? N : 1];
+
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int a = 0; a < N; ++a) acc[a] = 0ull;
+        if (COMP) {
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                hi[a] = 0ull;
+                lo[a] = 0ull;
+            }
+        }
+    }
+
+    // Add the two points (t.x, y.x), (t.y, y.y).  FIRST assigns instead of
+    // adding (the first pair of a compensated batch).
+    template <bool FIRST>
+    __device__ __forceinline__ void add_pair(u64 t, u64 y) {
+        u64 p = t;
+        if (FIRST) {
+            acc[2 * M] = y;
+            acc[0] = p;
+            acc[2 * M + 1] = mul2(p, y);
+        } else {
+            acc[2 * M] = add2(acc[2 * M], y);
+            acc[0] = add2(acc[0], p);
+            acc[2 * M + 1] = fma2(p, y, acc[2 * M + 1]);
+        }
+#pragma unroll
+        for (int k = 2; k <= 2 * M; ++k) {
+            p = mul2(p, t);
+            if (FIRST) {
+                acc[k - 1] = p;
+                if (k <= M) acc[2 * M + k] = mul2(p, y);
+            } else {
+                acc[k - 1] = add2(acc[k - 1], p);
+                if (k <= M) acc[2 * M + k] = fma2(p, y, acc[2 * M + k]);
+            }
+        }
+    }
+
+    // Compensated mode: move the batch sums into the (hi, lo) pairs.
+    __device__ __forceinline__ void fold() {
+        if (COMP) {
+#pragma unroll
+            for (int a = 0; a < N; ++a) fold2(hi[a], lo[a], acc[a]);
+        }
+    }
+
+    // Final per-thread value of accumulator a as double-float (both lanes).
+    __device__ __forceinline__ dflt result(int a) const {
+        float x0, x1;
+        dflt r;
+        if (COMP) {
+            float l0, l1;
+            up2(hi[a], x0, x1);
+            up2(lo[a], l0, l1);
+            dflt u = {x0, l0}, v = {x1, l1};
+            r = df_add(u, v);
+        } else {
+            up2(acc[a], x0, x1);
+            two_sum(x0, x1, r.hi, r.lo);
+        }
+        return r;
+    }
+};
+
+// FP64 accumulator.
+template <int M>
+struct AccF64 {
+    static constexpr int N = 3 * M + 1;
+    double acc[N];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int a = 0; a < N; ++a) acc[a] = 0.0;
+    }
+    __device__ __forceinline__ void add_point(double t, double y) {
+        double p = t;
+        acc[2 * M] += y;
+        acc[0] += p;
+        acc[2 * M + 1] = fma(p, y, acc[2 * M + 1]);
+#pragma unroll
+        for (int k = 2; k <= 2 * M; ++k) {
+            p *= t;
+            acc[k - 1] += p;
+            if (k <= M) acc[2 * M + k] = fma(p, y, acc[2 * M + k]);
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Reductions.  Values are reduced in a fixed order (the result depends only
+// on the launch shape, never on timing).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ dflt warp_reduce_df(dflt v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_reduce_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block reduction of N double-float accumulators held per thread; writes the
+// N block totals (as doubles) to out[] (shared or global), visible to all
+// threads after return.  `red` is shared scratch of kGroup * BLOCK dflt.
+// Groups of kGroup accumulators are transposed through shared memory: warp w
+// sums accumulator w of the group over all threads (strided, then a warp tree).
+template <int BLOCK, int N, typename GetF>
+__device__ __forceinline__ void block_reduce_df(GetF get, dflt* red, double* out) {
+    constexpr int kWarps = BLOCK / 32;
+    constexpr int kGroup = kWarps;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int g0 = 0; g0 < N; g0 += kGroup) {
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j)
+            if (g0 + j < N) red[j * BLOCK + tid] = get(g0 + j);
+        __syncthreads();
+        if (g0 + warp < N) {
+            dflt v = red[warp * BLOCK + lane];
+#pragma unroll
+            for (int i = 1; i < BLOCK / 32; ++i) v = df_add(v, red[warp * BLOCK + lane + 32 * i]);
+            v = warp_reduce_df(v);
+            if (lane == 0) out[g0 + warp] = df_to_double(v);
+        }
+        __syncthreads();
+    }
+}
+
+template <int BLOCK, int N, typename GetF>
+__device__ __forceinline__ void block_reduce_d(GetF get, double* red, double* out) {
+    constexpr int kWarps = BLOCK / 32;
+    constexpr int kGroup = kWarps;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int g0 = 0; g0 < N; g0 += kGroup) {
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j)
+            if (g0 + j < N) red[j * BLOCK + tid] = get(g0 + j);
+        __syncthreads();
+        if (g0 + warp < N) {
+            double v = red[warp * BLOCK + lane];
+#pragma unroll
+            for (int i = 1; i < BLOCK / 32; ++i) v += red[warp * BLOCK + lane + 32 * i];
+            v = warp_reduce_d(v);
+            if (lane == 0) out[g0 + warp] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 solve of the Hankel normal system (Section II) of runtime degree
+// m <= NMAX.  S = S_0..S_2m, T = T_0..T_m.  The (m+1)x(m+1) system is
+// embedded in an (NMAX+1)-square one as [[A, 0], [0, I]] so that lanes of a
+// warp solving systems of different degrees run the same instructions; the
+// padding changes no arithmetic on the real block (its entries only ever
+// meet zeros).  Partial pivoting takes the first row of largest magnitude;
+// a pivot at or below (m+1) * eps64 * max|A| is singular.  Writes ncoef
+// values of Xt (t basis, may be null) and X (x basis, by expanding
+// (s (x - c))^k): m+1 coefficients then zeros.  Returns an LSEFIT status;
+// on failure the m+1 coefficients are NaN.
+// ---------------------------------------------------------------------------
+// Gaussian elimination with partial pivoting of the padded system
+// [[A, 0], [0, I]] z = [rhs, 0] with A[j][k] = S[j+k] (j, k <= m).
+// Returns LSEFIT_OK or LSEFIT_ERR_SINGULAR; z[0..m] is the solution.
+template <int NMAX>
+__device__ __forceinline__ int hankel_ge(int m, const double* S, const double* rhs, double* z) {
+    constexpr int N = NMAX + 1;
+    int st = LSEFIT_OK;
+    double A[N][N + 1];
+    double amax = 0.0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            double v = (j == k) ? 1.0 : 0.0;
+            if (j <= m && k <= m) {
+                v = S[j + k];
+                amax = fmax(amax, fabs(v));
+            }
+            A[j][k] = v;
+        }
+        A[j][N] = (j <= m) ? rhs[j] : 0.0;
+    }
+    const double tol = (double)(m + 1) * 2.220446049250313e-16 * amax;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        int p = k;
+        double best = fabs(A[k][k]);
+#pragma unroll
+        for (int r = k + 1; r < N; ++r) {
+            const double v = fabs(A[r][k]);
+            if (v > best) {
+                best = v;
+                p = r;
+            }
+        }
+        if (k <= m && !(best > tol)) st = LSEFIT_ERR_SINGULAR;
+#pragma unroll
+        for (int r = k + 1; r < N; ++r) {
+            if (r == p) {
+#pragma unroll
+                for (int j = k; j <= N; ++j) {
+                    const double tmp = A[k][j];
+                    A[k][j] = A[r][j];
+                    A[r][j] = tmp;
+                }
+            }
+        }
+        const double inv = 1.0 / A[k][k];
+#pragma unroll
+        for (int r = k + 1; r < N; ++r) {
+            const double f = A[r][k] * inv;
+#pragma unroll
+            for (int j = k + 1; j <= N; ++j) A[r][j] = fma(-f, A[k][j], A[r][j]);
+        }
+    }
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+        double acc = A[i][N];
+#pragma unroll
+        for (int j = i + 1; j < N; ++j) acc = fma(-A[i][j], z[j], acc);
+        z[i] = acc / A[i][i];
+    }
+    if (st == LSEFIT_OK) {
+        bool zf = true;
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (i <= m) zf = zf && isfinite(z[i]);
+        if (!zf) st = LSEFIT_ERR_SINGULAR;
+    }
+    return st;
+}
+
+// Checks that precede the elimination: interval, point count, finiteness.
+__device__ __forceinline__ int fit_precheck(int m, const double* S, const double* T, bool map_ok) {
+    if (!map_ok) return LSEFIT_ERR_BAD_INTERVAL;
+    if (!(S[0] >= (double)(m + 1))) return LSEFIT_ERR_N_TOO_SMALL;
+    bool fin = true;
+    for (int k = 0; k <= 2 * m; ++k) fin = fin && isfinite(S[k]);
+    for (int k = 0; k <= m; ++k) fin = fin && isfinite(T[k]);
+    return fin ? LSEFIT_OK : LSEFIT_ERR_NONFINITE;
+}
+
+template <int NMAX>
+__device__ int solve_hankel_rt(int m, const double* S, const double* T, double c, double s,
+                               bool map_ok, double* Xt, double* X, int ncoef) {
+    constexpr int N = NMAX + 1;
+    double z[N];
+    int st = fit_precheck(m, S, T, map_ok);
+    if (st == LSEFIT_OK) st = hankel_ge<NMAX>(m, S, T, z);
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    if (st != LSEFIT_OK) {
+        for (int i = 0; i < ncoef; ++i) {
+            const double v = i <= m ? qnan : 0.0;
+            if (Xt) Xt[i] = v;
+            X[i] = v;
+        }
+        return st;
+    }
+    // un-map: X_j = sum_{k>=j} z_k C(k,j) s^k (-c)^(k-j), over k <= m only
+    double out[N];
+    double binom[N];  // row k of Pascal's triangle
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        out[j] = 0.0;
+        binom[j] = 0.0;
+    }
+    binom[0] = 1.0;
+    double sk = 1.0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        if (k > m) break;
+        if (k > 0) {
+#pragma unroll
+            for (int j = N - 1; j >= 1; --j) binom[j] += binom[j - 1];
+            sk *= s;
+        }
+        double cp = 1.0;  // (-c)^(k-j) as j runs from k down to 0
+#pragma unroll
+        for (int j = N - 1; j >= 0; --j) {
+            if (j <= k) {
+                out[j] = fma(z[k] * binom[j] * sk, cp, out[j]);
+                cp *= -c;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (i < ncoef) {
+            if (Xt) Xt[i] = i <= m ? z[i] : 0.0;
+            X[i] = i <= m ? out[i] : 0.0;
+        }
+    }
+    for (int i = N; i < ncoef; ++i) {
+        if (Xt) Xt[i] = 0.0;
+        X[i] = 0.0;
+    }
+    return LSEFIT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Accumulation of the points of one contiguous range [b, e) by `nthreads`
+// cooperating threads (`rank` = this thread's index among them): 16-byte
+// vectors of x and y when both start at the same offset within 16 bytes,
+// scalar loads for the unaligned head, the tail, and the rest otherwise.
+// ---------------------------------------------------------------------------
+template <int DT>
+__device__ __forceinline__ void split_range(const void* x, const void* y, int64_t b, int64_t e,
+                                            int64_t& head, int64_t& nvec) {
+    constexpr int ES = Elem<DT>::kSize, PV = Elem<DT>::kPerVec;
+    const uintptr_t xa = reinterpret_cast<uintptr_t>(x) + (uintptr_t)b * ES;
+    const uintptr_t ya = reinterpret_cast<uintptr_t>(y) + (uintptr_t)b * ES;
+    const int64_t len = e - b;
+    if ((xa & 15) == (ya & 15) && (xa % ES) == 0) {
+        int64_t h = (int64_t)(((16 - (xa & 15)) & 15) / ES);
+        head = h < len ? h : len;
+        nvec = (len - head) / PV;
+    } else {
+        head = len;
+        nvec = 0;
+    }
+}
+
+// Unpack one 16-byte vector of x and of y into packed pairs and feed them.
+template <int M, int DT, bool COMP, bool MAP, bool FIRST>
+__device__ __forceinline__ void feed_vec(AccF32<M, COMP>& A, uint4 xv, uint4 yv, u64 c2, u64 s2) {
+    if (DT == LSEFIT_F32) {
+        u64 xa = pk2(__uint_as_float(xv.x), __uint_as_float(xv.y));
+        u64 xb = pk2(__uint_as_float(xv.z), __uint_as_float(xv.w));
+        u64 ya = pk2(__uint_as_float(yv.x), __uint_as_float(yv.y));
+        u64 yb = pk2(__uint_as_float(yv.z), __uint_as_float(yv.w));
+        if (MAP) {
+            xa = mul2(sub2(xa, c2), s2);
+            xb = mul2(sub2(xb, c2), s2);
+        }
+        A.template add_pair<FIRST>(xa, ya);
+        A.template add_pair<false>(xb, yb);
+    } else {  // BF16: 8 points per vector
+        const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
+        const uint32_t yw[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            u64 xp = pk2(bf16_lo(xw[q]), bf16_hi(xw[q]));
+            u64 yp = pk2(bf16_lo(yw[q]), bf16_hi(yw[q]));
+            if (MAP) xp = mul2(sub2(xp, c2), s2);
+            if (q == 0) A.template add_pair<FIRST>(xp, yp);
+            else A.template add_pair<false>(xp, yp);
+        }
+    }
+}
+
+// FP32/BF16 storage, FP32 arithmetic.  In compensated mode each thread's
+// batch (UNROLL vectors, or one scalar point) is folded into its TwoSum pairs.
+template <int M, int DT, bool COMP, bool MAP, int UNROLL>
+__device__ __forceinline__ void accumulate_range(AccF32<M, COMP>& A, const void* x, const void* y,
+                                                 int64_t b, int64_t e, int64_t rank, int64_t nthreads,
+                                                 float cf, float sf) {
+    constexpr int ES = Elem<DT>::kSize, PV = Elem<DT>::kPerVec;
+    int64_t head, nvec;
+    split_range<DT>(x, y, b, e, head, nvec);
+    const u64 c2 = pk2(cf, cf), s2 = pk2(sf, sf);
+    const uint4* xv = reinterpret_cast<const uint4*>(static_cast<const char*>(x) + (b + head) * ES);
+    const uint4* yv = reinterpret_cast<const uint4*>(static_cast<const char*>(y) + (b + head) * ES);
+    int64_t v = rank;
+    for (; v + (UNROLL - 1) * nthreads < nvec; v += UNROLL * nthreads) {
+        uint4 xr[UNROLL], yr[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            xr[u] = ld_stream16(xv + v + u * nthreads);
+            yr[u] = ld_stream16(yv + v + u * nthreads);
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            if (u == 0) feed_vec<M, DT, COMP, MAP, COMP>(A, xr[u], yr[u], c2, s2);
+            else feed_vec<M, DT, COMP, MAP, false>(A, xr[u], yr[u], c2, s2);
+        }
+        A.fold();
+    }
+    for (; v < nvec; v += nthreads) {
+        feed_vec<M, DT, COMP, MAP, COMP>(A, ld_stream16(xv + v), ld_stream16(yv + v), c2, s2);
+        A.fold();
+    }
+    // scalar points: [b, b + head) and [b + head + nvec * PV, e)
+    const int64_t tail0 = b + head + nvec * PV;
+    const int64_t nscalar = head + (e - tail0);
+    for (int64_t q = rank; q < nscalar; q += nthreads) {
+        const int64_t i = q < head ? b + q : tail0 + (q - head);
+        float xs = Elem<DT>::ld(x, i);
+        const float ys = Elem<DT>::ld(y, i);
+        if (MAP) xs = __fmul_rn(__fsub_rn(xs, cf), sf);
+        A.template add_pair<COMP>(pk2(xs, 0.0f), pk2(ys, 0.0f));
+        A.fold();
+    }
+}
+
+// FP64 arithmetic for any storage.
+template <int DT, int PV>
+__device__ __forceinline__ void unpack_f64(uint4 r, double* v) {
+    if (DT == LSEFIT_F64) {
+        v[0] = __hiloint2double(r.y, r.x);
+        v[1] = __hiloint2double(r.w, r.z);
+    } else if (DT == LSEFIT_F32) {
+        v[0] = __uint_as_float(r.x);
+        v[1] = __uint_as_float(r.y);
+        v[2] = __uint_as_float(r.z);
+        v[3] = __uint_as_float(r.w);
+    } else {
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            v[2 * q] = bf16_lo(w[q]);
+            v[2 * q + 1] = bf16_hi(w[q]);
+        }
+    }
+}
+
+template <int M, int DT, int UNROLL, bool MAP>
+__device__ __forceinline__ void accumulate_range_f64(AccF64<M>& A, const void* x, const void* y,
+                                                     int64_t b, int64_t e, int64_t rank,
+                                                     int64_t nthreads, double c, double s) {
+    constexpr int ES = Elem<DT>::kSize, PV = Elem<DT>::kPerVec;
+    int64_t head, nvec;
+    split_range<DT>(x, y, b, e, head, nvec);
+    const uint4* xv = reinterpret_cast<const uint4*>(static_cast<const char*>(x) + (b + head) * ES);
+    const uint4* yv = reinterpret_cast<const uint4*>(static_cast<const char*>(y) + (b + head) * ES);
+    auto feed = [&](uint4 xr, uint4 yr) {
+        double xs[PV], ys[PV];
+        unpack_f64<DT, PV>(xr, xs);
+        unpack_f64<DT, PV>(yr, ys);
+#pragma unroll
+        for (int q = 0; q < PV; ++q) A.add_point(MAP ? s * (xs[q] - c) : xs[q], ys[q]);
+    };
+    int64_t v = rank;
+    for (; v + (UNROLL - 1) * nthreads < nvec; v += UNROLL * nthreads) {
+        uint4 xr[UNROLL], yr[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            xr[u] = ld_stream16(xv + v + u * nthreads);
+            yr[u] = ld_stream16(yv + v + u * nthreads);
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) feed(xr[u], yr[u]);
+    }
+    for (; v < nvec; v += nthreads) feed(ld_stream16(xv + v), ld_stream16(yv + v));
+    const int64_t tail0 = b + head + nvec * PV;
+    const int64_t nscalar = head + (e - tail0);
+    for (int64_t q = rank; q < nscalar; q += nthreads) {
+        const int64_t i = q < head ? b + q : tail0 + (q - head);
+        const double xs = Elem<DT>::ld64(x, i);
+        A.add_point(MAP ? s * (xs - c) : xs, Elem<DT>::ld64(y, i));
+    }
+}
+
+// Degree dispatch for runtime m.
+template <template <int> class F, typename... Args>
+__device__ __forceinline__ auto by_degree(int m, Args... args) {
+    switch (m) {
+        case 1: return F<1>::run(args...);
+        case 2: return F<2>::run(args...);
+        case 3: return F<3>::run(args...);
+        case 4: return F<4>::run(args...);
+        case 5: return F<5>::run(args...);
+        case 6: return F<6>::run(args...);
+        case 7: return F<7>::run(args...);
+        default: return F<8>::run(args...);
+    }
+}
+
+}  // namespace lsefit

@@ -1,0 +1,29 @@
+// lsefit_host.h -- host-side helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace lsefit {
+
+// Largest grid of the single-series reduction (bounds its workspace).
+constexpr int kMaxGrid = 4096;
+// Alignment of workspace regions.
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// SM count of the current device (cached per device).  Returns 0 on error.
+int current_sm_count(int* device_out);
+
+// Resident blocks per SM of `kernel` at `threads` threads and `smem` dynamic
+// shared memory (cached per kernel).  Returns at least 1.
+int occupancy_blocks(const void* kernel, int threads, size_t smem);
+
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+inline int elem_size(int dtype) { return dtype == 0 ? 8 : (dtype == 1 ? 4 : 2); }
+
+}  // namespace lsefit

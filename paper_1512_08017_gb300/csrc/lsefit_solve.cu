@@ -1,0 +1,46 @@
+// lsefit_solve.cu -- Gaussian elimination of the normal equations AX = B
+// (Section II), one system per thread, FP64, partial pivoting, followed by
+// the un-map of the coefficients.
+#include "lsefit_device.cuh"
+#include "lsefit_host.h"
+
+namespace lsefit {
+
+// One system per thread.  Systems of every degree up to NMAX share the
+// padded elimination, so a warp never diverges on the degree.
+template <int NMAX>
+__global__ void solve_kernel(const double* sums, int64_t count, int m_sums, int m,
+                             const double* map, double* X, double* Xt, int32_t* status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const double* row = sums + i * (3 * m_sums + 2);
+    double c = 0.0, s = 1.0;
+    bool ok = true;
+    if (map) {
+        c = map[2 * i];
+        s = map[2 * i + 1];
+        ok = isfinite(c) && isfinite(s) && s != 0.0;
+    }
+    const int st = solve_hankel_rt<NMAX>(m, row, row + 2 * m_sums + 1, c, s, ok,
+                                         Xt ? Xt + i * (m + 1) : nullptr, X + i * (m + 1), m + 1);
+    if (status) status[i] = st;
+}
+
+}  // namespace lsefit
+
+using namespace lsefit;
+
+extern "C" int lsefit_solve(const double* sums, int64_t count, int m_sums, int m, const double* map,
+                            double* X, double* Xt, int32_t* status, lsefit_stream_t stream) {
+    if (count < 0 || m < 1 || m > LSEFIT_MAX_DEGREE || m_sums < m || m_sums > LSEFIT_MAX_DEGREE)
+        return LSEFIT_ERR_INVALID_ARG;
+    if (count == 0) return LSEFIT_OK;
+    if (sums == nullptr || X == nullptr) return LSEFIT_ERR_INVALID_ARG;
+    const int threads = 64;
+    const int64_t blocks = (count + threads - 1) / threads;
+    if (blocks > 0x7fffffffll) return LSEFIT_ERR_INVALID_ARG;
+    auto k = m <= 1 ? solve_kernel<1> : m == 2 ? solve_kernel<2> : m == 3 ? solve_kernel<3>
+           : m <= 5 ? solve_kernel<5> : solve_kernel<8>;
+    k<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(sums, count, m_sums, m, map, X, Xt, status);
+    return cudaGetLastError() == cudaSuccess ? LSEFIT_OK : LSEFIT_ERR_CUDA;
+}
