@@ -61,7 +61,7 @@ enum {
     LSEFIT_OK = 0,
     LSEFIT_ERR_INVALID_ARG = 1,   /* host: a null pointer, size or enum out of range */
     LSEFIT_ERR_N_TOO_SMALL = 2,   /* per fit: n < m + 1 (the paper's n >= 2 only covers m = 1) */
-    LSEFIT_ERR_SINGULAR = 3,      /* per fit: a GE pivot <= (m+1) * eps64 * max|A| */
+    LSEFIT_ERR_SINGULAR = 3,      /* per fit: a GE pivot <= (m+1) * eps * max|A| (see lsefit_solve) */
     LSEFIT_ERR_NONFINITE = 4,     /* per fit: a power sum is Inf or NaN */
     LSEFIT_ERR_BAD_INTERVAL = 5,  /* per fit: interval not finite or hi <= lo */
     LSEFIT_ERR_WORKSPACE = 6,     /* host: workspace or plan buffer too small / misaligned */
@@ -137,14 +137,38 @@ int lsefit_powersums(const void* x, const void* y, int64_t n, int dtype, int m, 
  *  m_sums  degree the sums were accumulated for (row layout).
  *  m       degree to solve, 1 <= m <= m_sums: the sums of degree m_sums
  *          contain those of every lower degree, so one pass serves several.
+ *  accum   the LSEFIT_ACCUM_* the sums were formed with.  It sets the
+ *          singularity threshold: a pivot at or below (m+1) * eps * max|A|,
+ *          eps = 2^-52 for FP64 accumulation and 2^-23 otherwise (FP32
+ *          per-point powers leave pivots of that relative size in a
+ *          rank-deficient system).
  *  map     device double[count][2] {c, s} or NULL (identity).
  *  X       device double[count][m+1]: coefficients of x, ascending.
  *  Xt      device double[count][m+1] or NULL: coefficients of t.
  *  status  device int32[count] or NULL: LSEFIT_OK, _N_TOO_SMALL (S_0 < m+1),
  *          _NONFINITE, _SINGULAR or _BAD_INTERVAL (map not finite or s = 0).
  */
-int lsefit_solve(const double* sums, int64_t count, int m_sums, int m, const double* map,
-                 double* X, double* Xt, int32_t* status, lsefit_stream_t stream);
+int lsefit_solve(const double* sums, int64_t count, int m_sums, int m, int accum,
+                 const double* map, double* X, double* Xt, int32_t* status, lsefit_stream_t stream);
+
+/*
+ * lsefit_fit -- the whole single-series fit in one launch: the streaming
+ * pass of lsefit_powersums, then, in the block that completes the
+ * reduction, the Gaussian elimination of Section II for every degree
+ * d = m_lo..m from the same sums (the sums of degree m contain those of
+ * each lower degree), one degree per lane, followed by the un-map.
+ *  x..interval, workspace: as for lsefit_powersums.
+ *  m_lo    lowest degree to solve, 1 <= m_lo <= m.
+ *  X       device double[m-m_lo+1][m+1]: row r holds the x-basis
+ *          coefficients of degree m_lo+r, zero beyond that degree.
+ *  Xt      device, same shape, or NULL: t-basis coefficients.
+ *  sums    device double[3m+2] or NULL.
+ *  map     device double[2] or NULL.
+ *  status  device int32[m-m_lo+1]: per-degree status as for lsefit_solve.
+ */
+int lsefit_fit(const void* x, const void* y, int64_t n, int dtype, int m, int m_lo, int accum,
+               const double* interval, double* X, double* Xt, double* sums, double* map,
+               int32_t* status, void* workspace, size_t workspace_bytes, lsefit_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Batched ragged series (one persistent launch)

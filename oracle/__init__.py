@@ -33,6 +33,10 @@ _SRC = os.environ.get("LSEFIT_ORACLE_SOURCE") or os.path.join(_HERE, "lsefit_ora
 _BUILD_DIR = os.environ.get("LSEFIT_ORACLE_BUILD_DIR") or os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "liblsefit_oracle.so")
 
+# Machine epsilons of the arithmetic that formed the sums (singularity threshold).
+EPS64 = 2.0 ** -52
+EPS32 = 2.0 ** -23
+
 # Oracle status values, as numbered in lsefit_oracle.c.
 STATUS_NAMES = {0: "ok", 1: "n_too_small", 2: "singular", 3: "nonfinite",
                 4: "bad_interval", 5: "bad_arg"}
@@ -67,17 +71,17 @@ def _load():
         lib.orc_map_constants.restype = ctypes.c_int
         lib.orc_powersums.argtypes = [dp, dp, i64, ctypes.c_int, dp, dp, dp]
         lib.orc_powersums.restype = None
-        lib.orc_solve.argtypes = [ctypes.c_int, dp, dp, dp]
+        lib.orc_solve.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
         lib.orc_solve.restype = ctypes.c_int
         lib.orc_unmap.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp]
         lib.orc_unmap.restype = None
-        lib.orc_fit.argtypes = [dp, dp, i64, ctypes.c_int, dp, dp, dp, dp, dp]
+        lib.orc_fit.argtypes = [dp, dp, i64, ctypes.c_int, dp, ctypes.c_double, dp, dp, dp, dp]
         lib.orc_fit.restype = ctypes.c_int
         lib.orc_eval.argtypes = [ctypes.c_int, dp, dp, i64, dp]
         lib.orc_eval.restype = None
         lib.orc_sse.argtypes = [ctypes.c_int, dp, dp, dp, i64]
         lib.orc_sse.restype = ctypes.c_double
-        lib.orc_backward.argtypes = [dp, dp, i64, ctypes.c_int, dp, dp, dp, dp, dp, dp]
+        lib.orc_backward.argtypes = [dp, dp, i64, ctypes.c_int, dp, dp, dp, dp, ctypes.c_double, dp, dp]
         lib.orc_backward.restype = ctypes.c_int
         lib.orc_max_degree.argtypes = []
         lib.orc_max_degree.restype = ctypes.c_int
@@ -121,14 +125,15 @@ def powersums(x, y, m: int, cs=None):
     return S, T
 
 
-def solve(S, T, m: int):
+def solve(S, T, m: int, eps: float = EPS64):
     """Gaussian elimination (partial pivoting) of A X = B built from S, T.
 
+    eps: machine epsilon of the arithmetic that formed the sums.
     Returns (status_name, X)."""
     S = _f64(S)
     T = _f64(T)
     X = np.full(m + 1, np.nan)
-    st = _load().orc_solve(m, _ptr(S), _ptr(T), _ptr(X))
+    st = _load().orc_solve(m, _ptr(S), _ptr(T), float(eps), _ptr(X))
     return STATUS_NAMES[st], X
 
 
@@ -140,8 +145,9 @@ def unmap(Xt, c: float, s: float):
     return X
 
 
-def fit(x, y, m: int, cs=None) -> dict:
-    """The paper's fit.  Returns dict(status, X, Xt, S, T)."""
+def fit(x, y, m: int, cs=None, eps: float = EPS64) -> dict:
+    """The paper's fit.  eps: machine epsilon of the arithmetic the sums are
+    formed in (singularity threshold).  Returns dict(status, X, Xt, S, T)."""
     x = _f64(x)
     y = _f64(y)
     assert x.shape == y.shape and x.ndim == 1
@@ -151,18 +157,21 @@ def fit(x, y, m: int, cs=None) -> dict:
     T = np.zeros(m + 1)
     mp = _f64(cs) if cs is not None else None
     st = _load().orc_fit(_ptr(x), _ptr(y), x.size, m, _ptr(mp) if mp is not None else None,
-                         _ptr(X), _ptr(Xt), _ptr(S), _ptr(T))
+                         float(eps), _ptr(X), _ptr(Xt), _ptr(S), _ptr(T))
     return {"status": STATUS_NAMES[st], "X": X, "Xt": Xt, "S": S, "T": T}
 
 
 def fit_interval(x, y, m: int, lo: float, hi: float, fp32: bool) -> dict:
-    """Fit on t = s(x - c) for the map of [lo, hi] onto [-1, 1], coefficients mapped back."""
+    """Fit on t = s(x - c) for the map of [lo, hi] onto [-1, 1], coefficients mapped back.
+
+    fp32: the points are mapped and powered in FP32 (map constants rounded to
+    FP32, FP32 singularity threshold); otherwise FP64."""
     st, c, s = map_constants(lo, hi, fp32)
     if st != "ok":
         n = m + 1
         return {"status": st, "X": np.full(n, np.nan), "Xt": np.full(n, np.nan),
                 "S": None, "T": None, "c": np.nan, "s": np.nan}
-    out = fit(x, y, m, (c, s))
+    out = fit(x, y, m, (c, s), eps=EPS32 if fp32 else EPS64)
     out["c"] = c
     out["s"] = s
     return out
@@ -185,7 +194,7 @@ def sse(X, x, y) -> float:
     return float(_load().orc_sse(X.size - 1, _ptr(X), _ptr(x), _ptr(y), x.size))
 
 
-def backward(x, y, m: int, cs, S, Xt, gX):
+def backward(x, y, m: int, cs, S, Xt, gX, eps: float = EPS64):
     """Adjoint of ``fit`` for dL/dX = gX.  Returns (status_name, dx, dy)."""
     x = _f64(x)
     y = _f64(y)
@@ -196,5 +205,5 @@ def backward(x, y, m: int, cs, S, Xt, gX):
     dy = np.zeros_like(x)
     mp = _f64(cs) if cs is not None else None
     st = _load().orc_backward(_ptr(x), _ptr(y), x.size, m, _ptr(mp) if mp is not None else None,
-                              _ptr(S), _ptr(Xt), _ptr(gX), _ptr(dx), _ptr(dy))
+                              _ptr(S), _ptr(Xt), _ptr(gX), float(eps), _ptr(dx), _ptr(dy))
     return STATUS_NAMES[st], dx, dy

@@ -22,8 +22,11 @@
  *   - the last row of A is printed with x^(m+2) in its second column; the
  *     Hankel rule A[j][k] = S_{j+k} is used;
  *   - "Gaussian elimination" carries no pivoting rule: partial pivoting with
- *     the first row of largest magnitude, and a pivot below
- *     (m+1)*eps64*max|A| reported as singular;
+ *     the first row of largest magnitude, and a pivot at or below
+ *     (m+1)*eps*max|A| reported as singular, where eps is the machine epsilon
+ *     of the arithmetic that formed the power sums (2^-52 for FP64, 2^-23
+ *     for FP32 per-point powers: their rounding alone leaves pivots of that
+ *     relative size in a rank-deficient system);
  *   - n >= 2 is only enough for m = 1: n >= m+1 is required.
  * Not in the paper (the precision extension of the method):
  *   - an affine map t = s*(x - c) of the abscissae, with c = (lo+hi)/2 and
@@ -100,14 +103,14 @@ void orc_powersums(const double* x, const double* y, int64_t n, int m,
 
 /* Gaussian elimination with partial pivoting of the (m+1)x(m+1) system
  * M z = r, M row-major; M and r are overwritten.  Returns ORC_SINGULAR when
- * a pivot is at or below (m+1)*eps64*max|M|. */
-static int orc_gauss_inplace(int m, double* M, double* r, double* z)
+ * a pivot is at or below (m+1)*eps*max|M|. */
+static int orc_gauss_inplace(int m, double* M, double* r, double* z, double eps)
 {
     const int N = m + 1;
     double amax = 0.0;
     for (int i = 0; i < N * N; ++i)
         if (fabs(M[i]) > amax) amax = fabs(M[i]);
-    const double tol = (double)N * DBL_EPSILON * amax;
+    const double tol = (double)N * eps * amax;
     for (int k = 0; k < N; ++k) {
         int p = k;
         for (int i = k + 1; i < N; ++i)
@@ -140,8 +143,9 @@ static int orc_gauss_inplace(int m, double* M, double* r, double* z)
 }
 
 /* Section II: A[j][k] = S[j+k], B[j] = T[j]; solve AX = B by Gaussian
- * elimination.  Checks finiteness of the sums first. */
-int orc_solve(int m, const double* S, const double* T, double* X)
+ * elimination.  Checks finiteness of the sums first.  eps: machine epsilon
+ * of the arithmetic that formed the sums (singularity threshold). */
+int orc_solve(int m, const double* S, const double* T, double eps, double* X)
 {
     if (m < 1 || m > ORC_MAX_M) return ORC_BAD_ARG;
     const int N = m + 1;
@@ -155,7 +159,7 @@ int orc_solve(int m, const double* S, const double* T, double* X)
         for (int k = 0; k < N; ++k) A[j * N + k] = S[j + k];
         B[j] = T[j];
     }
-    return orc_gauss_inplace(m, A, B, X);
+    return orc_gauss_inplace(m, A, B, X, eps);
 }
 
 /* Binomial coefficient C(k, j) as a double (exact for k <= 16). */
@@ -191,11 +195,11 @@ static void orc_unmap_transpose(int m, double c, double s, const double* gX, dou
 
 /*
  * The whole fit: power sums, normal equations, Gaussian elimination, un-map.
- * map = {c, s} or NULL.  Outputs (any may be NULL except X): X (x basis),
+ * map = {c, s} or NULL; eps as for orc_solve.  Outputs (any may be NULL except X): X (x basis),
  * Xt (t basis), S[2m+1], T[m+1].  Returns an ORC_* status; on failure X and
  * Xt are NaN.
  */
-int orc_fit(const double* x, const double* y, int64_t n, int m, const double* map,
+int orc_fit(const double* x, const double* y, int64_t n, int m, const double* map, double eps,
             double* X, double* Xt, double* S_out, double* T_out)
 {
     double S[2 * ORC_MAX_M + 1], T[ORC_MAX_M + 1], Z[ORC_MAX_M + 1];
@@ -205,7 +209,7 @@ int orc_fit(const double* x, const double* y, int64_t n, int m, const double* ma
     if (T_out) memcpy(T_out, T, sizeof(double) * (m + 1));
     int st = ORC_OK;
     if (n < m + 1) st = ORC_N_TOO_SMALL;
-    else st = orc_solve(m, S, T, Z);
+    else st = orc_solve(m, S, T, eps, Z);
     if (st != ORC_OK) {
         for (int j = 0; j <= m; ++j) {
             X[j] = NAN;
@@ -259,7 +263,7 @@ double orc_sse(int m, const double* X, const double* x, const double* y, int64_t
  * S holds the t-basis power sums S_0..S_2m, Xt the t-basis coefficients.
  */
 int orc_backward(const double* x, const double* y, int64_t n, int m, const double* map,
-                 const double* S, const double* Xt, const double* gX,
+                 const double* S, const double* Xt, const double* gX, double eps,
                  double* dx, double* dy)
 {
     double gt[ORC_MAX_M + 1], A[(ORC_MAX_M + 1) * (ORC_MAX_M + 1)], lam[ORC_MAX_M + 1];
@@ -269,7 +273,7 @@ int orc_backward(const double* x, const double* y, int64_t n, int m, const doubl
     else memcpy(gt, gX, sizeof(double) * N);
     for (int j = 0; j < N; ++j)
         for (int k = 0; k < N; ++k) A[j * N + k] = S[j + k];
-    int st = orc_gauss_inplace(m, A, gt, lam);
+    int st = orc_gauss_inplace(m, A, gt, lam, eps);
     if (st != ORC_OK) return st;
     const double sc = map ? map[1] : 1.0;
     for (int64_t i = 0; i < n; ++i) {

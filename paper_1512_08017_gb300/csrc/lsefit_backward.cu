@@ -34,6 +34,9 @@ struct BwParams {
     const double* Xt;       // [S][m_max+1]
     const double* map;      // [S][2] or null
     const double* lambda;   // [S][m_max+1] (workspace)
+    const float* lamf;      // [S][m_max+1] FP32 copies for the FP32 point pass (workspace)
+    const float* xtf;       // [S][m_max+1]
+    const float2* mapf;     // [S] (c, s) as FP32
     const int32_t* status;  // [S]
     const int4* block_tasks;
     int n_block_tasks;
@@ -45,15 +48,23 @@ struct BwParams {
 // ---------------------------------------------------------------------------
 // launch 1: lambda per series
 // ---------------------------------------------------------------------------
+// Also writes FP32 copies of lambda, Xt and (c, s) so that the point pass of
+// FP32 data runs no FP64 instruction (FP64 is 1/64 rate on GB300).
 template <int NMAX>
-__global__ void lambda_kernel(int64_t S, int m_max, const int32_t* degree, const double* sums,
-                              const double* map, const double* gX, double* lambda, int32_t* status) {
+__global__ void lambda_kernel(int64_t S, int m_max, double eps, const int32_t* degree, const double* sums,
+                              const double* map, const double* gX, const double* Xt, double* lambda,
+                              float* lamf, float* xtf, float2* mapf, int32_t* status) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     const int nc = m_max + 1;
     const int m = degree[s];
     double* lam = lambda + s * nc;
-    for (int j = 0; j < nc; ++j) lam[j] = 0.0;
+    for (int j = 0; j < nc; ++j) {
+        lam[j] = 0.0;
+        lamf[s * nc + j] = 0.0f;
+        xtf[s * nc + j] = (float)Xt[s * nc + j];
+    }
+    mapf[s] = map ? make_float2((float)map[2 * s], (float)map[2 * s + 1]) : make_float2(0.0f, 1.0f);
     if (m < 1 || m > m_max || m > NMAX) {
         status[s] = LSEFIT_ERR_INVALID_ARG;
         return;
@@ -100,12 +111,16 @@ __global__ void lambda_kernel(int64_t S, int m_max, const int32_t* degree, const
         bool fin = true;
 #pragma unroll
         for (int k = 0; k < N; ++k) fin = fin && isfinite(gt[k]);
-        st = fin ? hankel_ge<NMAX>(m, Srow, gt, z) : LSEFIT_ERR_NONFINITE;
+        st = fin ? hankel_ge<NMAX>(m, Srow, gt, z, eps) : LSEFIT_ERR_NONFINITE;
     }
     if (st == LSEFIT_OK) {
 #pragma unroll
-        for (int j = 0; j < N; ++j)
-            if (j <= m) lam[j] = z[j];
+        for (int j = 0; j < N; ++j) {
+            if (j <= m) {
+                lam[j] = z[j];
+                lamf[s * nc + j] = (float)z[j];
+            }
+        }
     }
     status[s] = st;
 }
@@ -144,17 +159,16 @@ __device__ __forceinline__ void grad_pair(const u64* lam, const u64* xt, u64 t, 
 
 template <int M, int DT>
 __device__ __forceinline__ void grad_range_f32(const BwParams& p, int64_t b, int64_t e, int64_t rank,
-                                               int64_t nthreads, const double* lam64, const double* xt64,
-                                               double c, double sc) {
+                                               int64_t nthreads, const float* lam32, const float* xt32,
+                                               float cf, float sf) {
     constexpr int ES = Elem<DT>::kSize, PV = Elem<DT>::kPerVec;
     u64 lam[M + 1], xt[M + 1];
 #pragma unroll
     for (int j = 0; j <= M; ++j) {
-        const float l = (float)lam64[j], f = (float)xt64[j];
+        const float l = lam32[j], f = xt32[j];
         lam[j] = pk2(l, l);
         xt[j] = pk2(f, f);
     }
-    const float cf = (float)c, sf = (float)sc;
     const u64 c2 = pk2(cf, cf), s2 = pk2(sf, sf);
     float* dx = static_cast<float*>(p.dx);
     float* dy = static_cast<float*>(p.dy);
@@ -244,11 +258,11 @@ template <int DT, int M>
 __device__ __forceinline__ void grad_task(const BwParams& p, int64_t s, int64_t b, int64_t e, int64_t rank,
                                           int64_t nthreads) {
     const int nc = p.m_max + 1;
-    const double* lam = p.lambda + s * nc;
-    const double* xt = p.Xt + s * nc;
-    const double c = p.map ? p.map[2 * s] : 0.0;
-    const double sc = p.map ? p.map[2 * s + 1] : 1.0;
     if constexpr (DT == LSEFIT_F64) {
+        const double* lam = p.lambda + s * nc;
+        const double* xt = p.Xt + s * nc;
+        const double c = p.map ? p.map[2 * s] : 0.0;
+        const double sc = p.map ? p.map[2 * s + 1] : 1.0;
         double l[M + 1], f[M + 1];
 #pragma unroll
         for (int j = 0; j <= M; ++j) {
@@ -257,13 +271,8 @@ __device__ __forceinline__ void grad_task(const BwParams& p, int64_t s, int64_t 
         }
         grad_range_f64<M>(p, b, e, rank, nthreads, l, f, c, sc);
     } else {
-        double l[M + 1], f[M + 1];
-#pragma unroll
-        for (int j = 0; j <= M; ++j) {
-            l[j] = lam[j];
-            f[j] = xt[j];
-        }
-        grad_range_f32<M, DT>(p, b, e, rank, nthreads, l, f, c, sc);
+        const float2 cs = p.mapf[s];
+        grad_range_f32<M, DT>(p, b, e, rank, nthreads, p.lamf + s * nc, p.xtf + s * nc, cs.x, cs.y);
     }
 }
 
@@ -328,9 +337,20 @@ __global__ void __launch_bounds__(kBwBlock) grad_kernel(BwParams p) {
 
 using namespace lsefit;
 
-extern "C" size_t lsefit_backward_workspace_size(const lsefit_plan* plan) {
-    if (plan == nullptr || plan->m_max < 1) return 0;
+// Workspace: counters | lambda [S][m_max+1] FP64 | lambda, Xt [S][m_max+1] FP32 | (c, s) [S] FP32.
+static size_t bw_off_lamf(const lsefit_plan* plan) {
     return kAlign + align_up((size_t)plan->num_series * (plan->m_max + 1) * sizeof(double), kAlign);
+}
+static size_t bw_off_xtf(const lsefit_plan* plan) {
+    return bw_off_lamf(plan) + align_up((size_t)plan->num_series * (plan->m_max + 1) * sizeof(float), kAlign);
+}
+static size_t bw_off_mapf(const lsefit_plan* plan) {
+    return bw_off_xtf(plan) + align_up((size_t)plan->num_series * (plan->m_max + 1) * sizeof(float), kAlign);
+}
+
+extern "C" size_t lsefit_backward_workspace_size(const lsefit_plan* plan) {
+    if (plan == nullptr || plan->m_max < 1 || plan->num_series < 0) return 0;
+    return bw_off_mapf(plan) + align_up((size_t)plan->num_series * sizeof(float2), kAlign);
 }
 
 extern "C" int lsefit_backward(const lsefit_batch* batch, const lsefit_plan* plan, const double* sums,
@@ -343,6 +363,7 @@ extern "C" int lsefit_backward(const lsefit_batch* batch, const lsefit_plan* pla
         b.m_max > LSEFIT_MAX_DEGREE)
         return LSEFIT_ERR_INVALID_ARG;
     if (b.dtype < LSEFIT_F64 || b.dtype > LSEFIT_BF16) return LSEFIT_ERR_INVALID_ARG;
+    if (b.accum < LSEFIT_ACCUM_NAIVE || b.accum > LSEFIT_ACCUM_F64) return LSEFIT_ERR_INVALID_ARG;
     if (b.num_series == 0) return LSEFIT_OK;
     if (sums == nullptr || Xt == nullptr || gX == nullptr || b.offsets == nullptr || b.degree == nullptr)
         return LSEFIT_ERR_INVALID_ARG;
@@ -353,11 +374,15 @@ extern "C" int lsefit_backward(const lsefit_batch* batch, const lsefit_plan* pla
         return LSEFIT_ERR_WORKSPACE;
     char* ws = static_cast<char*>(workspace);
     double* lambda = reinterpret_cast<double*>(ws + kAlign);
+    float* lamf = reinterpret_cast<float*>(ws + bw_off_lamf(plan));
+    float* xtf = reinterpret_cast<float*>(ws + bw_off_xtf(plan));
+    float2* mapf = reinterpret_cast<float2*>(ws + bw_off_mapf(plan));
     const int threads = 64;
     const int64_t blocks = (b.num_series + threads - 1) / threads;
     auto lk = b.m_max <= 3 ? lambda_kernel<3> : b.m_max <= 5 ? lambda_kernel<5> : lambda_kernel<8>;
-    lk<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(b.num_series, b.m_max, b.degree, sums, map, gX,
-                                                              lambda, status);
+    lk<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(b.num_series, b.m_max, singular_eps(b.accum),
+                                                              b.degree, sums, map, gX, Xt, lambda, lamf, xtf,
+                                                              mapf, status);
     if (cudaGetLastError() != cudaSuccess) return LSEFIT_ERR_CUDA;
 
     BwParams p;
@@ -372,6 +397,9 @@ extern "C" int lsefit_backward(const lsefit_batch* batch, const lsefit_plan* pla
     p.Xt = Xt;
     p.map = map;
     p.lambda = lambda;
+    p.lamf = lamf;
+    p.xtf = xtf;
+    p.mapf = mapf;
     p.status = status;
     p.block_tasks = reinterpret_cast<const int4*>(plan->block_tasks);
     p.n_block_tasks = plan->n_block_tasks;

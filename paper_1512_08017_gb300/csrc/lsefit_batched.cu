@@ -98,11 +98,20 @@ extern "C" int lsefit_plan_build(const int64_t* offsets, int64_t num_series, int
     return LSEFIT_OK;
 }
 
+// Workspace: queue counters | tickets [nbt] | FP64 chunk partials [nbt][3m_max+1]
+// | prepared map constants [num_series] (16 bytes each).
+static size_t ws_tickets_off() { return kAlign; }
+static size_t ws_partials_off(const lsefit_plan* plan) {
+    return ws_tickets_off() + align_up((size_t)plan->n_block_tasks * sizeof(unsigned), kAlign);
+}
+static size_t ws_map_off(const lsefit_plan* plan) {
+    return ws_partials_off(plan) +
+           align_up((size_t)plan->n_block_tasks * (size_t)(3 * plan->m_max + 1) * sizeof(double), kAlign);
+}
+
 extern "C" size_t lsefit_batched_workspace_size(const lsefit_plan* plan) {
-    if (plan == nullptr) return 0;
-    const size_t nbt = plan->n_block_tasks > 0 ? (size_t)plan->n_block_tasks : 0;
-    return kAlign + align_up(nbt * sizeof(unsigned), kAlign) +
-           align_up(nbt * (size_t)(3 * plan->m_max + 1) * sizeof(double), kAlign);
+    if (plan == nullptr || plan->n_block_tasks < 0 || plan->num_series < 0) return 0;
+    return ws_map_off(plan) + align_up((size_t)plan->num_series * 16, kAlign);
 }
 
 extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* plan, double* X,
@@ -144,11 +153,12 @@ extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* 
     p.sums = sums;
     p.map = map;
     p.status = status;
+    p.eps = singular_eps(b.accum);
     char* ws = static_cast<char*>(workspace);
     p.counters = reinterpret_cast<unsigned*>(ws);
-    p.tickets = reinterpret_cast<unsigned*>(ws + kAlign);
-    p.partials = reinterpret_cast<double*>(
-        ws + kAlign + align_up((size_t)plan->n_block_tasks * sizeof(unsigned), kAlign));
+    p.tickets = reinterpret_cast<unsigned*>(ws + ws_tickets_off());
+    p.partials = reinterpret_cast<double*>(ws + ws_partials_off(plan));
+    p.mapc = reinterpret_cast<double2*>(ws + ws_map_off(plan));
 
     const int nmax = b.m_max <= 5 ? 5 : 8;
     batched_kernel_t k = pick_batched(b.dtype, b.accum, nmax);
@@ -175,6 +185,13 @@ extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* 
     const int64_t useful = (int64_t)plan->n_block_tasks + (plan->n_warp_tasks + kBWarps - 1) / kBWarps;
     if (useful < grid) grid = useful;
     if (grid < 1) grid = 1;
+    {
+        const int pt = 256;
+        const int64_t pb = (b.num_series + pt - 1) / pt;
+        auto prep = b.accum == LSEFIT_ACCUM_F64 ? batched_prep_kernel<false> : batched_prep_kernel<true>;
+        prep<<<(unsigned)pb, pt, 0, (cudaStream_t)stream>>>(p);
+        if (cudaGetLastError() != cudaSuccess) return LSEFIT_ERR_CUDA;
+    }
     k<<<(unsigned)grid, kBBlock, smem, (cudaStream_t)stream>>>(p);
     return cudaGetLastError() == cudaSuccess ? LSEFIT_OK : LSEFIT_ERR_CUDA;
 }

@@ -326,6 +326,72 @@ __device__ __forceinline__ void block_reduce_df(GetF get, dflt* red, double* out
     }
 }
 
+// As block_reduce_df, but the block totals stay double-float (no FP64
+// instruction: on GB300 FP64 runs at 1/64 of the FP32 rate).
+template <int BLOCK, int N, typename GetF>
+__device__ __forceinline__ void block_reduce_df2(GetF get, dflt* red, dflt* out) {
+    constexpr int kWarps = BLOCK / 32;
+    constexpr int kGroup = kWarps;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int g0 = 0; g0 < N; g0 += kGroup) {
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j)
+            if (g0 + j < N) red[j * BLOCK + tid] = get(g0 + j);
+        __syncthreads();
+        if (g0 + warp < N) {
+            dflt v = red[warp * BLOCK + lane];
+#pragma unroll
+            for (int i = 1; i < BLOCK / 32; ++i) v = df_add(v, red[warp * BLOCK + lane + 32 * i]);
+            v = warp_reduce_df(v);
+            if (lane == 0) out[g0 + warp] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// Warp reduce-scatter by recursive halving: v[0..NP) per lane (entries at
+// or beyond the caller's count are zero); on return lane l holds the warp
+// total of entry (l mod NP).  At the level of half-size H each lane keeps
+// the half of its entries picked by lane bit H and receives the partner's
+// copy of that half, so NP-1 exchanges replace the NP*5 of a butterfly per
+// entry.  NP is 16 or 32.
+template <int NP>
+__device__ __forceinline__ dflt warp_reduce_scatter_df(dflt* v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int H = NP / 2; H >= 1; H /= 2) {
+        const bool upper = (lane & H) != 0;
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            const dflt keep = upper ? v[H + i] : v[i];
+            const dflt send = upper ? v[i] : v[H + i];
+            v[i] = df_add(keep, df_shfl_xor(send, H));
+        }
+    }
+#pragma unroll
+    for (int o = NP; o < 32; o *= 2) v[0] = df_add(v[0], df_shfl_xor(v[0], o));
+    return v[0];
+}
+
+template <int NP>
+__device__ __forceinline__ double warp_reduce_scatter_d(double* v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int H = NP / 2; H >= 1; H /= 2) {
+        const bool upper = (lane & H) != 0;
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            const double keep = upper ? v[H + i] : v[i];
+            const double send = upper ? v[i] : v[H + i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, H);
+        }
+    }
+#pragma unroll
+    for (int o = NP; o < 32; o *= 2) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    return v[0];
+}
+
 template <int BLOCK, int N, typename GetF>
 __device__ __forceinline__ void block_reduce_d(GetF get, double* red, double* out) {
     constexpr int kWarps = BLOCK / 32;
@@ -355,16 +421,23 @@ __device__ __forceinline__ void block_reduce_d(GetF get, double* red, double* ou
 // warp solving systems of different degrees run the same instructions; the
 // padding changes no arithmetic on the real block (its entries only ever
 // meet zeros).  Partial pivoting takes the first row of largest magnitude;
-// a pivot at or below (m+1) * eps64 * max|A| is singular.  Writes ncoef
+// a pivot at or below (m+1) * eps * max|A| is singular (eps: singular_eps).  Writes ncoef
 // values of Xt (t basis, may be null) and X (x basis, by expanding
 // (s (x - c))^k): m+1 coefficients then zeros.  Returns an LSEFIT status;
 // on failure the m+1 coefficients are NaN.
 // ---------------------------------------------------------------------------
+// Machine epsilon of the arithmetic that formed the power sums: a pivot at
+// or below (m+1) * eps * max|A| is treated as zero.  FP32 per-point powers
+// alone leave pivots of relative size ~2^-24 in a rank-deficient system.
+__host__ __device__ constexpr double singular_eps(int accum) {
+    return accum == LSEFIT_ACCUM_F64 ? 2.220446049250313e-16 : 1.1920928955078125e-07;
+}
+
 // Gaussian elimination with partial pivoting of the padded system
 // [[A, 0], [0, I]] z = [rhs, 0] with A[j][k] = S[j+k] (j, k <= m).
 // Returns LSEFIT_OK or LSEFIT_ERR_SINGULAR; z[0..m] is the solution.
 template <int NMAX>
-__device__ __forceinline__ int hankel_ge(int m, const double* S, const double* rhs, double* z) {
+__device__ __forceinline__ int hankel_ge(int m, const double* S, const double* rhs, double* z, double eps) {
     constexpr int N = NMAX + 1;
     int st = LSEFIT_OK;
     double A[N][N + 1];
@@ -382,7 +455,8 @@ __device__ __forceinline__ int hankel_ge(int m, const double* S, const double* r
         }
         A[j][N] = (j <= m) ? rhs[j] : 0.0;
     }
-    const double tol = (double)(m + 1) * 2.220446049250313e-16 * amax;
+    const double tol = (double)(m + 1) * eps * amax;
+    double inv_piv[N];  // reciprocal of each pivot, reused by the back-substitution
 #pragma unroll
     for (int k = 0; k < N; ++k) {
         int p = k;
@@ -408,6 +482,7 @@ __device__ __forceinline__ int hankel_ge(int m, const double* S, const double* r
             }
         }
         const double inv = 1.0 / A[k][k];
+        inv_piv[k] = inv;
 #pragma unroll
         for (int r = k + 1; r < N; ++r) {
             const double f = A[r][k] * inv;
@@ -420,7 +495,7 @@ __device__ __forceinline__ int hankel_ge(int m, const double* S, const double* r
         double acc = A[i][N];
 #pragma unroll
         for (int j = i + 1; j < N; ++j) acc = fma(-A[i][j], z[j], acc);
-        z[i] = acc / A[i][i];
+        z[i] = acc * inv_piv[i];
     }
     if (st == LSEFIT_OK) {
         bool zf = true;
@@ -444,11 +519,11 @@ __device__ __forceinline__ int fit_precheck(int m, const double* S, const double
 
 template <int NMAX>
 __device__ int solve_hankel_rt(int m, const double* S, const double* T, double c, double s,
-                               bool map_ok, double* Xt, double* X, int ncoef) {
+                               bool map_ok, double eps, double* Xt, double* X, int ncoef) {
     constexpr int N = NMAX + 1;
     double z[N];
     int st = fit_precheck(m, S, T, map_ok);
-    if (st == LSEFIT_OK) st = hankel_ge<NMAX>(m, S, T, z);
+    if (st == LSEFIT_OK) st = hankel_ge<NMAX>(m, S, T, z, eps);
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
     if (st != LSEFIT_OK) {
         for (int i = 0; i < ncoef; ++i) {

@@ -26,6 +26,12 @@ struct PSParams {
     int32_t* status;
     double* partials;       // [gridDim.x][3m+1]
     unsigned int* ticket;   // zero between calls
+    // fused solve (lsefit_fit): degrees m_lo..m, one per lane of warp 0
+    int m_lo;
+    double eps;             // singularity threshold epsilon of the accumulation
+    double* X;              // [m-m_lo+1][m+1] or null (no solve)
+    double* Xt;             // same shape or null
+    int32_t* fit_status;    // [m-m_lo+1]
 };
 
 // Last block: fixed-order FP64 sum of the per-block partials, then the outputs.
@@ -33,6 +39,7 @@ template <int M>
 __device__ void ps_finish(const PSParams& p, bool map_ok, double c, double s, double* comb) {
     constexpr int N = 3 * M + 1;
     constexpr int J = kPSBlock / N;
+    __shared__ double tot_s[N + 1];
     const int tid = threadIdx.x;
     const int G = gridDim.x;
     if (tid < N * J) {
@@ -48,16 +55,31 @@ __device__ void ps_finish(const PSParams& p, bool map_ok, double c, double s, do
         for (int j = 0; j < J; ++j) tot += comb[tid * J + j];
         // accumulator a holds S_{a+1} (a < 2M) or T_{a-2M}; in the output
         // layout S_0..S_2M, T_0..T_M both land at index a + 1.
-        p.sums[tid + 1] = map_ok ? tot : qnan;
+        tot_s[tid + 1] = map_ok ? tot : qnan;
+        if (p.sums) p.sums[tid + 1] = map_ok ? tot : qnan;
     }
     if (tid == 0) {
-        p.sums[0] = map_ok ? (double)p.n : qnan;
+        tot_s[0] = map_ok ? (double)p.n : qnan;
+        if (p.sums) p.sums[0] = map_ok ? (double)p.n : qnan;
         if (p.map_out) {
             p.map_out[0] = map_ok ? c : qnan;
             p.map_out[1] = map_ok ? s : qnan;
         }
         if (p.status) p.status[0] = map_ok ? LSEFIT_OK : LSEFIT_ERR_BAD_INTERVAL;
         *p.ticket = 0u;  // ready for the next call
+    }
+    if (p.X != nullptr) {
+        // every requested degree d = m_lo + lane solves from the prefix of the
+        // degree-M sums (S_0..S_2d, T_0..T_d), all lanes in step
+        __syncthreads();
+        const int lane = tid;
+        if (tid < 32 && lane <= M - p.m_lo) {
+            const int d = p.m_lo + lane;
+            const int st = solve_hankel_rt<M>(d, tot_s, tot_s + 2 * M + 1, c, s, map_ok, p.eps,
+                                              p.Xt ? p.Xt + lane * (M + 1) : nullptr, p.X + lane * (M + 1),
+                                              M + 1);
+            p.fit_status[lane] = st;
+        }
     }
 }
 
@@ -181,10 +203,13 @@ extern "C" size_t lsefit_powersums_workspace_size(int m) {
     return kAlign + align_up((size_t)kMaxGrid * (3 * m + 1) * sizeof(double), kAlign);
 }
 
-extern "C" int lsefit_powersums(const void* x, const void* y, int64_t n, int dtype, int m, int accum,
-                                const double* interval, double* sums, double* map, int32_t* status,
-                                void* workspace, size_t workspace_bytes, lsefit_stream_t stream) {
-    if (m < 1 || m > LSEFIT_MAX_DEGREE || n < 0 || sums == nullptr) return LSEFIT_ERR_INVALID_ARG;
+static int launch_powersums(const void* x, const void* y, int64_t n, int dtype, int m, int accum,
+                            const double* interval, double* sums, double* map, int32_t* status,
+                            void* workspace, size_t workspace_bytes, lsefit_stream_t stream, int m_lo,
+                            double* X, double* Xt, int32_t* fit_status) {
+    if (m < 1 || m > LSEFIT_MAX_DEGREE || n < 0) return LSEFIT_ERR_INVALID_ARG;
+    if (sums == nullptr && X == nullptr) return LSEFIT_ERR_INVALID_ARG;
+    if (X != nullptr && (m_lo < 1 || m_lo > m || fit_status == nullptr)) return LSEFIT_ERR_INVALID_ARG;
     if (dtype < LSEFIT_F64 || dtype > LSEFIT_BF16) return LSEFIT_ERR_INVALID_ARG;
     if (accum < LSEFIT_ACCUM_NAIVE || accum > LSEFIT_ACCUM_F64) return LSEFIT_ERR_INVALID_ARG;
     if (dtype == LSEFIT_F64 && accum != LSEFIT_ACCUM_F64) return LSEFIT_ERR_UNSUPPORTED;
@@ -208,6 +233,11 @@ extern "C" int lsefit_powersums(const void* x, const void* y, int64_t n, int dty
     p.status = status;
     p.ticket = static_cast<unsigned int*>(workspace);
     p.partials = reinterpret_cast<double*>(static_cast<char*>(workspace) + kAlign);
+    p.m_lo = m_lo;
+    p.eps = singular_eps(accum);
+    p.X = X;
+    p.Xt = Xt;
+    p.fit_status = fit_status;
 
     ps_kernel_t k = pick_kernel(m, dtype, accum, interval != nullptr);
     int dev = 0;
@@ -223,4 +253,20 @@ extern "C" int lsefit_powersums(const void* x, const void* y, int64_t n, int dty
     if (grid > kMaxGrid) grid = kMaxGrid;
     k<<<(unsigned)grid, kPSBlock, 0, (cudaStream_t)stream>>>(p);
     return cudaGetLastError() == cudaSuccess ? LSEFIT_OK : LSEFIT_ERR_CUDA;
+}
+
+extern "C" int lsefit_powersums(const void* x, const void* y, int64_t n, int dtype, int m, int accum,
+                                const double* interval, double* sums, double* map, int32_t* status,
+                                void* workspace, size_t workspace_bytes, lsefit_stream_t stream) {
+    if (sums == nullptr) return LSEFIT_ERR_INVALID_ARG;
+    return launch_powersums(x, y, n, dtype, m, accum, interval, sums, map, status, workspace, workspace_bytes,
+                            stream, 0, nullptr, nullptr, nullptr);
+}
+
+extern "C" int lsefit_fit(const void* x, const void* y, int64_t n, int dtype, int m, int m_lo, int accum,
+                          const double* interval, double* X, double* Xt, double* sums, double* map,
+                          int32_t* status, void* workspace, size_t workspace_bytes, lsefit_stream_t stream) {
+    if (X == nullptr || status == nullptr) return LSEFIT_ERR_INVALID_ARG;
+    return launch_powersums(x, y, n, dtype, m, accum, interval, sums, map, nullptr, workspace, workspace_bytes,
+                            stream, m_lo, X, Xt, status);
 }

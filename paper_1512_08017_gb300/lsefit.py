@@ -82,7 +82,8 @@ SIGNATURES = {
     "lsefit_abi_version": (_INT, []),
     "lsefit_powersums_workspace_size": (_SZ, [_INT]),
     "lsefit_powersums": (_INT, [_VP, _VP, _I64, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
-    "lsefit_solve": (_INT, [_VP, _I64, _INT, _INT, _VP, _VP, _VP, _VP, _VP]),
+    "lsefit_solve": (_INT, [_VP, _I64, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP]),
+    "lsefit_fit": (_INT, [_VP, _VP, _I64, _INT, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "lsefit_plan_build": (_INT, [_VP, _I64, _INT, _VP, _INT, _VP, _VP, _I64, _VP, _I64]),
     "lsefit_batched_workspace_size": (_SZ, [_VP]),
     "lsefit_fit_batched": (_INT, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
@@ -215,11 +216,12 @@ def powersums(x: torch.Tensor, y: torch.Tensor, m: int, accum="comp", interval=N
     return sums, map_out, status
 
 
-def solve(sums: torch.Tensor, m: int, m_sums: int | None = None, map=None, *, X=None, Xt=None,
+def solve(sums: torch.Tensor, m: int, m_sums: int | None = None, map=None, accum="comp", *, X=None, Xt=None,
           status=None, stream=None):
     """Gaussian elimination of the normal equations (lsefit_solve).
 
-    sums: [count, 3*m_sums+2] or [3*m_sums+2] float64 CUDA tensor.
+    sums: [count, 3*m_sums+2] or [3*m_sums+2] float64 CUDA tensor; accum: the
+    accumulation the sums were formed with (sets the singularity threshold).
     Returns (X, Xt, status) with X, Xt [count, m+1] (or [m+1])."""
     single = sums.dim() == 1
     S = sums.reshape(1, -1) if single else sums
@@ -235,8 +237,8 @@ def solve(sums: torch.Tensor, m: int, m_sums: int | None = None, map=None, *, X=
         Xt = torch.empty(count, m + 1, dtype=torch.float64, device=dev)
     if status is None:
         status = torch.empty(count, dtype=torch.int32, device=dev)
-    rc = lib.lsefit_solve(_ptr(S), count, int(m_sums), int(m), _ptr(map), _ptr(X), _ptr(Xt),
-                          _ptr(status), ctypes.c_void_p(_stream_handle(stream)))
+    rc = lib.lsefit_solve(_ptr(S), count, int(m_sums), int(m), _accum_code(accum), _ptr(map), _ptr(X),
+                          _ptr(Xt), _ptr(status), ctypes.c_void_p(_stream_handle(stream)))
     _check(rc, "lsefit_solve")
     if single:
         return X.reshape(-1), Xt.reshape(-1), status
@@ -244,10 +246,39 @@ def solve(sums: torch.Tensor, m: int, m_sums: int | None = None, map=None, *, X=
 
 
 def fit(x: torch.Tensor, y: torch.Tensor, m: int, accum="comp", interval=None, stream=None) -> dict:
-    """One series: power sums then Gaussian elimination.  Device tensors out."""
+    """One series: power sums then Gaussian elimination (two launches).  Device tensors out."""
     sums, mp, st0 = powersums(x, y, m, accum, interval, stream=stream)
-    X, Xt, st = solve(sums, m, m, mp, stream=stream)
+    X, Xt, st = solve(sums, m, m, mp, accum, stream=stream)
     return {"X": X, "Xt": Xt, "sums": sums, "map": mp, "status": st}
+
+
+def fit_degrees(x: torch.Tensor, y: torch.Tensor, m: int, m_lo: int = 1, accum="comp", interval=None, *,
+                out: dict | None = None, stream=None) -> dict:
+    """One series, every degree m_lo..m from one pass, in one launch (lsefit_fit).
+
+    Returns dict(X [m-m_lo+1, m+1], Xt, sums [3m+2], map [2], status [m-m_lo+1])."""
+    if x.dim() != 1 or x.shape != y.shape or x.dtype != y.dtype:
+        raise ValueError("x and y must be 1-D tensors of the same shape and dtype")
+    if not (x.is_cuda or x.is_pinned()) or not (y.is_cuda or y.is_pinned()):
+        raise ValueError("x and y must be CUDA tensors or pinned host tensors")
+    if not (1 <= m_lo <= m <= MAX_DEGREE):
+        raise ValueError(f"need 1 <= m_lo <= m <= {MAX_DEGREE}")
+    dev = _device_of(x)
+    sh = _stream_handle(stream)
+    iv = _interval_tensor(interval, dev)
+    k = m - m_lo + 1
+    if out is None:
+        out = {"X": torch.empty(k, m + 1, dtype=torch.float64, device=dev),
+               "Xt": torch.empty(k, m + 1, dtype=torch.float64, device=dev),
+               "sums": torch.empty(3 * m + 2, dtype=torch.float64, device=dev),
+               "map": torch.empty(2, dtype=torch.float64, device=dev),
+               "status": torch.empty(k, dtype=torch.int32, device=dev)}
+    ws = workspace("powersums", lib.lsefit_powersums_workspace_size(m), dev, sh)
+    rc = lib.lsefit_fit(_ptr(x), _ptr(y), x.numel(), _dtype_code(x), int(m), int(m_lo), _accum_code(accum),
+                        _ptr(iv), _ptr(out["X"]), _ptr(out.get("Xt")), _ptr(out.get("sums")),
+                        _ptr(out.get("map")), _ptr(out["status"]), _ptr(ws), ws.numel(), ctypes.c_void_p(sh))
+    _check(rc, "lsefit_fit")
+    return out
 
 
 def status_names(status: torch.Tensor):

@@ -66,7 +66,8 @@ def test_argument_errors_before_any_cuda_call(L):
     assert lib.lsefit_powersums(None, None, 0, L.F32, 2, 1, None, sums, None, None, ws, 0, None) == L.ERR_WORKSPACE
     # solve: nothing to do for count 0; degree checks
     X = (ctypes.c_double * 16)()
-    assert lib.lsefit_solve(sums, 0, 3, 3, None, X, None, None, None) == L.OK
-    assert lib.lsefit_solve(sums, 1, 2, 3, None, X, None, None, None) == L.ERR_INVALID_ARG
-    assert lib.lsefit_solve(sums, 1, 9, 3, None, X, None, None, None) == L.ERR_INVALID_ARG
-    assert lib.lsefit_solve(sums, -1, 3, 3, None, X, None, None, None) == L.ERR_INVALID_ARG
+    assert lib.lsefit_solve(sums, 0, 3, 3, 1, None, X, None, None, None) == L.OK
+    assert lib.lsefit_solve(sums, 1, 2, 3, 1, None, X, None, None, None) == L.ERR_INVALID_ARG
+    assert lib.lsefit_solve(sums, 1, 9, 3, 1, None, X, None, None, None) == L.ERR_INVALID_ARG
+    assert lib.lsefit_solve(sums, -1, 3, 3, 1, None, X, None, None, None) == L.ERR_INVALID_ARG
+    assert lib.lsefit_solve(sums, 1, 3, 3, 7, None, X, None, None, None) == L.ERR_INVALID_ARG

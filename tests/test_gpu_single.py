@@ -235,3 +235,32 @@ def test_mapped_host_memory(L):
     ref = oracle.fit(d["x"], d["y"], 3)
     assert L.status_names(out["status"]) == ["ok"]
     assert _rel(out["X"].cpu().numpy(), ref["X"]) <= 1e-5
+
+
+# --- fused single-launch fit of several degrees (lsefit_fit) ------------------------------
+
+@pytest.mark.parametrize("m,m_lo", [(3, 1), (5, 2), (8, 8), (1, 1)])
+def test_fused_fit_degrees(L, m, m_lo):
+    d = synth.single_large(n=(1 << 20) + 3, m=min(m, 4), seed=60 + m)
+    x, y = _dev(d["x"]), _dev(d["y"])
+    out = L.fit_degrees(x, y, m, m_lo, accum="comp", interval=(-1.0, 1.0))
+    assert L.status_names(out["status"]) == ["ok"] * (m - m_lo + 1)
+    X = out["X"].cpu().numpy()
+    Xt = out["Xt"].cpu().numpy()
+    for r, deg in enumerate(range(m_lo, m + 1)):
+        ref = oracle.fit_interval(d["x"], d["y"], deg, -1.0, 1.0, fp32=True)
+        cond = np.linalg.cond(_hankel(ref["S"], deg))
+        tol = 1e-5 if deg <= 3 else cond * EPS32 * 4 * deg
+        assert _rel(Xt[r, : deg + 1], ref["Xt"]) <= tol, (deg, cond)
+        assert np.all(X[r, deg + 1:] == 0.0)
+        # same as the two-launch path
+        X2, Xt2, st2 = L.solve(out["sums"], deg, m, out["map"])
+        assert _rel(Xt[r, : deg + 1], Xt2.cpu().numpy()) <= 1e-12
+
+
+def test_fused_fit_statuses(L):
+    f32 = torch.float32
+    out = L.fit_degrees(_dev(np.linspace(-1, 1, 3), f32), _dev(np.ones(3), f32), 4, 1)
+    assert L.status_names(out["status"]) == ["ok", "ok", "n_too_small", "n_too_small"]
+    out = L.fit_degrees(_dev(np.linspace(-1, 1, 30), f32), _dev(np.ones(30), f32), 2, 1, interval=(3.0, 1.0))
+    assert L.status_names(out["status"]) == ["bad_interval", "bad_interval"]
