@@ -49,6 +49,8 @@ def parse_args(argv=None):
     p.add_argument("--workload", default="single_large",
                    choices=["single_large", "ragged_batch", "diff_batch", "single_fp64"])
     p.add_argument("--n", type=int, default=1 << 28, help="points of the single_large series")
+    p.add_argument("--series", type=int, default=65536, help="series of the ragged_batch workload")
+    p.add_argument("--no-plain", action="store_true", help="skip the plain per-series comparison")
     p.add_argument("--accum", default="comp", choices=["comp", "naive", "f64"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -324,6 +326,371 @@ def run_single_large(args, dist: Dist):
     return line
 
 
+# ---------------------------------------------------------------------------
+# shared timing helpers for the batched workloads
+# ---------------------------------------------------------------------------
+def _event_steps(step, steps, stream):
+    """Per-step CUDA-event durations (ms) and the total (ms) of `steps` calls of step()."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for a, b in evs:
+        a.record(stream)
+        step()
+        b.record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs], t0.elapsed_time(t1)
+
+
+def _graph(fn, stream):
+    """Capture fn() (after one warm call on a side stream) into a CUDA graph."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        fn()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    return g
+
+
+def _roofline(algo_bytes, kern_ms, kernel, key):
+    peaks, peak_kind = measured_peaks()
+    achieved = algo_bytes / (kern_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": recorded_traffic(key), "kernel": kernel,
+            "kernel_ms": kern_ms,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+            else "fallback 6800 GB/s"}
+
+
+# ---------------------------------------------------------------------------
+# ragged_batch: 65,536 independent series of uneven length and mixed degree
+# ---------------------------------------------------------------------------
+def run_ragged_batch(args, dist: Dist):
+    import ctypes
+    import torch
+    import synth
+    import paper_1512_08017_gb300 as L
+    from paper_1512_08017_gb300 import autotune, lsefit as B
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    b = synth.ragged_batch(num_series=args.series, seed=synth.SEED_RAGGED + dist.rank)
+    S = len(b["degree"])
+    N = int(b["offsets"][-1])
+    m_max = 5
+    hx = torch.from_numpy(b["x"]).pin_memory()
+    hy = torch.from_numpy(b["y"]).pin_memory()
+    x, y = hx.to(dev), hy.to(dev)
+    off = torch.from_numpy(b["offsets"]).to(dev)
+    deg = torch.from_numpy(b["degree"]).to(dev)
+    iv = torch.from_numpy(b["interval"]).to(dev)
+    t_tune = time.perf_counter()
+    tuning, tried = autotune.tune_batched(x, y, off, deg, iv, m_max=m_max, accum=args.accum)
+    t_tune = time.perf_counter() - t_tune
+    t_plan = time.perf_counter()
+    plan = L.BatchPlan(b["offsets"], m_max, tuning=tuning, device=dev)
+    t_plan = time.perf_counter() - t_plan
+    out = {"X": torch.empty(S, m_max + 1, dtype=torch.float64, device=dev),
+           "status": torch.empty(S, dtype=torch.int32, device=dev)}
+    stream = torch.cuda.current_stream()
+
+    def fwd():
+        L.fit_batched(x, y, off, deg, iv, m_max=m_max, accum=args.accum, plan=plan, out=out)
+
+    g = _graph(fwd, stream)
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    assert int((out["status"] != 0).sum().item()) == 0
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    per, total = _event_steps(g.replay, args.steps, stream)
+    dist.barrier()
+    clk = clocks.stop()
+    ms = dist.max(total)
+    step_ms = dist.max(statistics.mean(per))
+    per_series_bytes = 8 + 4 + 16 + 8 * (m_max + 1) + 4
+    algo = 8 * N + per_series_bytes * S
+
+    # plain per-series path: one single-series fit launch per series from a host loop
+    plain = None
+    if not args.no_plain:
+        wsz = L.lib.lsefit_powersums_workspace_size(m_max)
+        ws = torch.zeros(wsz, dtype=torch.uint8, device=dev)
+        Xp = torch.empty(S, m_max + 1, dtype=torch.float64, device=dev)
+        stp = torch.empty(S, dtype=torch.int32, device=dev)
+        fn = B.lib.lsefit_fit
+        xs, ys, ivp = x.data_ptr(), y.data_ptr(), iv.data_ptr()
+        sh = ctypes.c_void_p(stream.cuda_stream)
+        calls = []
+        for s_ in range(S):
+            lo, hi = int(b["offsets"][s_]), int(b["offsets"][s_ + 1])
+            m = int(b["degree"][s_])
+            calls.append((ctypes.c_void_p(xs + 4 * lo), ctypes.c_void_p(ys + 4 * lo), hi - lo, B.F32, m, m,
+                          B.ACCUM[args.accum], ctypes.c_void_p(ivp + 16 * s_),
+                          ctypes.c_void_p(Xp.data_ptr() + 8 * (m_max + 1) * s_), None, None, None,
+                          ctypes.c_void_p(stp.data_ptr() + 4 * s_), ctypes.c_void_p(ws.data_ptr()), wsz, sh))
+
+        def plain_step():
+            for c_ in calls:
+                fn(*c_)
+
+        plain_step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        w0 = time.perf_counter()
+        e0.record(stream)
+        plain_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        pms = e0.elapsed_time(e1)
+        plain = {"value": N / (pms / 1e3), "unit": UNIT, "ms_per_step": pms, "host_wall_s": wall,
+                 "launches_per_step": S, "desc": "one lsefit_fit launch per series from a host loop, no graph"}
+
+    e2e = None
+    if not args.no_e2e:
+        hX = torch.empty(S, m_max + 1, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            x.copy_(hx, non_blocking=True)
+            y.copy_(hy, non_blocking=True)
+            g.replay()
+            hX.copy_(out["X"], non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        _, e_total = _event_steps(e2e_step, 3, stream)
+        e_ms = dist.max(e_total) / 3
+        e2e = {"value": dist.world * N / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": 8 * N,
+               "d2h_bytes_per_step": 8 * (m_max + 1) * S, "ms_per_step": e_ms}
+
+    cpu = None
+    if dist.rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        rng = np.random.default_rng(7)
+        pick = rng.choice(S, min(S, 3000), replace=False)
+        pts = 0
+        t0 = time.perf_counter()
+        for s_ in pick:
+            lo, hi = int(b["offsets"][s_]), int(b["offsets"][s_ + 1])
+            r = oracle.fit_interval(b["x"][lo:hi], b["y"][lo:hi], int(b["degree"][s_]), *b["interval"][s_],
+                                    fp32=True)
+            pts += hi - lo
+        dt = time.perf_counter() - t0
+        cpu = {"value": pts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{len(pick)} random series of the batch ({pts} points), oracle fit per series, "
+                         f"{dt:.1f} s"}
+    return {
+        "metric": "fitted points/s (fwd, batched ragged)", "value": dist.world * N * args.steps / (ms / 1e3),
+        "unit": UNIT, "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded ragged batch)",
+        "config": {"workload": f"batched ragged: {S} series, lengths log-uniform 16..65536, degrees 1..5, "
+                               "per-series intervals; one persistent launch in a CUDA graph",
+                   "series": S, "points": N, "accum": args.accum, "tuning": tuning,
+                   "autotune_s": t_tune, "plan_build_s": t_plan, "autotune_candidates": len(tried),
+                   "l2": f"inputs ({8 * N / 1e9:.1f} GB) larger than L2; no flush"},
+        "hbm_gbs": algo / (step_ms / 1e3) / 1e9,
+        "roofline": _roofline(algo, step_ms, "batched_kernel<5,F32,comp> (+ prep launch)", "batched_f32_comp"),
+        "plain_per_series": plain,
+        "speedup_vs_plain": (plain["ms_per_step"] / (ms / args.steps)) if plain else None,
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": 2 * args.steps,
+    }
+
+
+# ---------------------------------------------------------------------------
+# diff_batch: 4,096 series x 4,096 points, forward + hand-written backward
+# ---------------------------------------------------------------------------
+def run_diff_batch(args, dist: Dist):
+    import ctypes
+    import torch
+    import synth
+    import paper_1512_08017_gb300 as L
+    from paper_1512_08017_gb300 import lsefit as B
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d = synth.diff_batch(seed=synth.SEED_DIFF + dist.rank)
+    S, n = d["x"].shape
+    N = S * n
+    m = 3
+    x = torch.from_numpy(d["x"].reshape(-1)).to(dev)
+    y = torch.from_numpy(d["y"].reshape(-1)).to(dev)
+    offsets = np.arange(S + 1, dtype=np.int64) * n
+    off = torch.from_numpy(offsets).to(dev)
+    deg = torch.full((S,), m, dtype=torch.int32, device=dev)
+    iv = torch.tensor([[-1.0, 1.0]] * S, dtype=torch.float64, device=dev)
+    w = torch.from_numpy(d["w"]).to(dev)
+    plan = L.BatchPlan(offsets, m, tuning={"warp_max_len": 1024, "chunk_len": 4096}, device=dev)
+    fwd_out = {"X": torch.empty(S, m + 1, dtype=torch.float64, device=dev),
+               "Xt": torch.empty(S, m + 1, dtype=torch.float64, device=dev),
+               "sums": torch.empty(S, 3 * m + 2, dtype=torch.float64, device=dev),
+               "map": torch.empty(S, 2, dtype=torch.float64, device=dev),
+               "status": torch.empty(S, dtype=torch.int32, device=dev)}
+    dx = torch.empty_like(x)
+    dy = torch.empty_like(y)
+    bst = torch.empty(S, dtype=torch.int32, device=dev)
+    gX = torch.empty(S, m + 1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def fwd():
+        L.fit_batched(x, y, off, deg, iv, m_max=m, accum=args.accum, plan=plan, out=fwd_out)
+
+    def fwd_bwd():
+        fwd()
+        torch.mul(fwd_out["X"], w, out=gX)
+        gX.mul_(2.0)  # dL/dX of L = sum w X^2 (the user's loss)
+        L.backward(x, y, off, deg, fwd_out, gX, dx=dx, dy=dy, status=bst, accum=args.accum)
+
+    gf = _graph(fwd, stream)
+    gb = _graph(fwd_bwd, stream)
+    for _ in range(args.warmup):
+        gf.replay()
+        gb.replay()
+    torch.cuda.synchronize()
+    assert int((bst != 0).sum().item()) == 0
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    perf, totf = _event_steps(gf.replay, args.steps, stream)
+    perb, totb = _event_steps(gb.replay, args.steps, stream)
+    dist.barrier()
+    clk = clocks.stop()
+    msf = dist.max(totf) / args.steps
+    msb = dist.max(totb) / args.steps
+    plain = None
+    if not args.no_plain:
+        # one single-series forward and one single-series backward launch pair per series
+        plan1 = L.BatchPlan(np.array([0, n], dtype=np.int64), m, device=dev)
+        wsz = L.lib.lsefit_powersums_workspace_size(m)
+        ws = torch.zeros(wsz, dtype=torch.uint8, device=dev)
+        bws = torch.zeros(L.lib.lsefit_backward_workspace_size(ctypes.byref(plan1.plan)), dtype=torch.uint8,
+                          device=dev)
+        off1 = torch.tensor([0, n], dtype=torch.int64, device=dev)
+        deg1 = torch.tensor([m], dtype=torch.int32, device=dev)
+        Xs = torch.empty(S, m + 1, dtype=torch.float64, device=dev)
+        Xts = torch.empty(S, m + 1, dtype=torch.float64, device=dev)
+        sums = torch.empty(S, 3 * m + 2, dtype=torch.float64, device=dev)
+        mp = torch.empty(S, 2, dtype=torch.float64, device=dev)
+        st = torch.empty(S, dtype=torch.int32, device=dev)
+        sh = ctypes.c_void_p(stream.cuda_stream)
+        batches = []
+        for s_ in range(S):
+            bb = B.Batch(x.data_ptr() + 4 * n * s_, y.data_ptr() + 4 * n * s_, off1.data_ptr(), deg1.data_ptr(),
+                         None, 1, m, B.F32, B.ACCUM[args.accum], 0)
+            batches.append(bb)
+
+        def plain_step():
+            for s_ in range(S):
+                B.lib.lsefit_fit(ctypes.c_void_p(x.data_ptr() + 4 * n * s_), ctypes.c_void_p(y.data_ptr() + 4 * n * s_),
+                                 n, B.F32, m, m, B.ACCUM[args.accum], ctypes.c_void_p(iv.data_ptr() + 16 * s_),
+                                 ctypes.c_void_p(Xs.data_ptr() + 8 * (m + 1) * s_),
+                                 ctypes.c_void_p(Xts.data_ptr() + 8 * (m + 1) * s_),
+                                 ctypes.c_void_p(sums.data_ptr() + 8 * (3 * m + 2) * s_),
+                                 ctypes.c_void_p(mp.data_ptr() + 16 * s_), ctypes.c_void_p(st.data_ptr() + 4 * s_),
+                                 ctypes.c_void_p(ws.data_ptr()), wsz, sh)
+            torch.mul(Xs, w, out=gX)
+            gX.mul_(2.0)
+            for s_ in range(S):
+                B.lib.lsefit_backward(ctypes.byref(batches[s_]), ctypes.byref(plan1.plan),
+                                      ctypes.c_void_p(sums.data_ptr() + 8 * (3 * m + 2) * s_),
+                                      ctypes.c_void_p(Xts.data_ptr() + 8 * (m + 1) * s_),
+                                      ctypes.c_void_p(mp.data_ptr() + 16 * s_),
+                                      ctypes.c_void_p(gX.data_ptr() + 8 * (m + 1) * s_),
+                                      ctypes.c_void_p(dx.data_ptr() + 4 * n * s_),
+                                      ctypes.c_void_p(dy.data_ptr() + 4 * n * s_),
+                                      ctypes.c_void_p(bst.data_ptr() + 4 * s_), ctypes.c_void_p(bws.data_ptr()),
+                                      bws.numel(), sh)
+
+        plain_step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plain_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1)
+        plain = {"value": N / (pms / 1e3), "unit": UNIT, "ms_per_step": pms, "launches_per_step": 4 * S,
+                 "desc": "per series: one lsefit_fit and one lsefit_backward call from a host loop, no graph"}
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.from_numpy(d["x"].reshape(-1)).pin_memory()
+        hy = torch.from_numpy(d["y"].reshape(-1)).pin_memory()
+        hdx = torch.empty(N, dtype=torch.float32).pin_memory()
+        hdy = torch.empty(N, dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            x.copy_(hx, non_blocking=True)
+            y.copy_(hy, non_blocking=True)
+            gb.replay()
+            hdx.copy_(dx, non_blocking=True)
+            hdy.copy_(dy, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        _, e_total = _event_steps(e2e_step, 3, stream)
+        e_ms = dist.max(e_total) / 3
+        e2e = {"value": dist.world * N / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": 8 * N,
+               "d2h_bytes_per_step": 8 * N, "ms_per_step": e_ms}
+    return {
+        "metric": "fitted points/s (fwd+bwd)", "value": dist.world * N / (msb / 1e3), "unit": UNIT,
+        "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": msb,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded)",
+        "config": {"workload": "differentiable fit: 4096 series x 4096 FP32 points, degree 3, "
+                               "L = sum w X^2; forward + backward in one CUDA graph",
+                   "series": S, "points": N, "accum": args.accum, "tuning": plan.tuning},
+        "fwd": {"value": dist.world * N / (msf / 1e3), "unit": UNIT, "ms_per_step": msf,
+                "hbm_gbs": 8 * N / (msf / 1e3) / 1e9},
+        "fwd_bwd_hbm_gbs": 24 * N / (msb / 1e3) / 1e9,
+        "roofline": _roofline(24 * N, msb, "batched forward + lambda + grad kernels", "diff_fwd_bwd"),
+        "plain_per_series": plain,
+        "speedup_vs_plain": (plain["ms_per_step"] / msb) if plain else None,
+        "cpu_baseline": None, "e2e": e2e, "clocks": clk, "gpu_launches": 6 * args.steps,
+    }
+
+
+# ---------------------------------------------------------------------------
+# single_fp64: the plain method on 100,000 FP64 points, degrees 1-3 in one launch
+# ---------------------------------------------------------------------------
+def run_single_fp64(args, dist: Dist):
+    import torch
+    import synth
+    import paper_1512_08017_gb300 as L
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d = synth.single_fp64(seed=synth.SEED_SINGLE_FP64 + dist.rank)
+    n = d["x"].size
+    x = torch.from_numpy(d["x"]).to(dev)
+    y = torch.from_numpy(d["y"]).to(dev)
+    out = L.fit_degrees(x, y, 3, 1, "f64")
+    stream = torch.cuda.current_stream()
+    g = _graph(lambda: L.fit_degrees(x, y, 3, 1, "f64", out=out), stream)
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    per, total = _event_steps(g.replay, args.steps, stream)
+    ms = dist.max(total) / args.steps
+    return {"metric": "fit latency (FP64, degrees 1-3 in one launch)", "value": ms * 1e3, "unit": "us",
+            "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)", "points_per_s": n / (ms / 1e3),
+            "config": {"workload": "single series, n=100,000 FP64, x ~ U[0,10], degrees 1,2,3", "n": n},
+            "gpu_launches": args.steps}
+
+
 def run_reference(args, dist: Dist):
     """The oracle timed on the host cores on the same workload and metric."""
     if dist.rank != 0:
@@ -372,11 +739,9 @@ def main(argv=None):
         return 1
     dist = Dist(args.gpus)
     try:
-        if args.workload == "single_large":
-            line = run_single_large(args, dist)
-        else:
-            import bench_workloads  # noqa: F401  (added with the batched paths)
-            line = bench_workloads.run(args, dist)
+        runners = {"single_large": run_single_large, "ragged_batch": run_ragged_batch,
+                   "diff_batch": run_diff_batch, "single_fp64": run_single_fp64}
+        line = runners[args.workload](args, dist)
         if dist.rank == 0 and line is not None:
             print(json.dumps(line))
     finally:

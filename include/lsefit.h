@@ -24,11 +24,12 @@
  *    singular or non-finite system, a bad interval) are written per fit to a
  *    device int32 status array with the same codes; coefficients of a
  *    failed fit are NaN.
- *  - Workspaces must be zero-filled once before their first use.  Every
- *    call leaves its workspace zero-filled again where it needs zeros, so a
- *    workspace can be reused by later calls on the same stream (and by CUDA
- *    graph replays).  Two calls that run at the same time must not share a
- *    workspace.
+ *  - Workspaces are caller-provided scratch.  The single-series workspace
+ *    must be zero-filled once before its first use; every call leaves it
+ *    zeroed again, so it can be reused by later calls on the same stream
+ *    (and by CUDA graph replays).  The batched and backward workspaces need
+ *    no initialization (their first launch clears what must start at zero).
+ *    Two calls that run at the same time must not share a workspace.
  *  - Affine map.  When an interval [lo, hi] is given, every abscissa is
  *    mapped to t = s (x - c) with c = (lo + hi) / 2, s = 2 / (hi - lo),
  *    computed in FP64 and rounded once to the precision the points are
@@ -254,8 +255,8 @@ size_t lsefit_batched_workspace_size(const lsefit_plan* plan);
  *            lsefit_backward), rest zero.
  *  map       device double[num_series][2] or NULL: {c, s} used per series.
  *  status    device int32[num_series]: per-series status.
- *  workspace device, >= lsefit_batched_workspace_size(plan), zero-filled before
- *            first use.
+ *  workspace device, >= lsefit_batched_workspace_size(plan), 256-byte aligned;
+ *            no initialization needed.
  */
 int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* plan, double* X,
                        double* Xt, double* sums, double* map, int32_t* status,
@@ -293,8 +294,8 @@ size_t lsefit_backward_workspace_size(const lsefit_plan* plan);
  *            adjoint system has no solution (_N_TOO_SMALL, _NONFINITE,
  *            _SINGULAR, _BAD_INTERVAL, _INVALID_ARG for a bad degree); such
  *            series get zero gradients.
- *  workspace device, >= lsefit_backward_workspace_size(plan), 256-byte aligned,
- *            zero-filled before first use.
+ *  workspace device, >= lsefit_backward_workspace_size(plan), 256-byte aligned;
+ *            no initialization needed.
  */
 int lsefit_backward(const lsefit_batch* batch, const lsefit_plan* plan, const double* sums,
                     const double* Xt, const double* map, const double* gX, void* dx, void* dy,

@@ -53,8 +53,9 @@ struct BwParams {
 template <int NMAX>
 __global__ void lambda_kernel(int64_t S, int m_max, double eps, const int32_t* degree, const double* sums,
                               const double* map, const double* gX, const double* Xt, double* lambda,
-                              float* lamf, float* xtf, float2* mapf, int32_t* status) {
+                              float* lamf, float* xtf, float2* mapf, int32_t* status, unsigned* counters) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < 3) counters[s] = 0u;  // the point pass's queue counters (no initialization needed)
     if (s >= S) return;
     const int nc = m_max + 1;
     const int m = degree[s];
@@ -382,7 +383,7 @@ extern "C" int lsefit_backward(const lsefit_batch* batch, const lsefit_plan* pla
     auto lk = b.m_max <= 3 ? lambda_kernel<3> : b.m_max <= 5 ? lambda_kernel<5> : lambda_kernel<8>;
     lk<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(b.num_series, b.m_max, singular_eps(b.accum),
                                                               b.degree, sums, map, gX, Xt, lambda, lamf, xtf,
-                                                              mapf, status);
+                                                              mapf, status, reinterpret_cast<unsigned*>(ws));
     if (cudaGetLastError() != cudaSuccess) return LSEFIT_ERR_CUDA;
 
     BwParams p;

@@ -187,7 +187,8 @@ extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* 
     if (grid < 1) grid = 1;
     {
         const int pt = 256;
-        const int64_t pb = (b.num_series + pt - 1) / pt;
+        const int64_t items = std::max<int64_t>(std::max<int64_t>(b.num_series, plan->n_block_tasks), 3);
+        const int64_t pb = (items + pt - 1) / pt;
         auto prep = b.accum == LSEFIT_ACCUM_F64 ? batched_prep_kernel<false> : batched_prep_kernel<true>;
         prep<<<(unsigned)pb, pt, 0, (cudaStream_t)stream>>>(p);
         if (cudaGetLastError() != cudaSuccess) return LSEFIT_ERR_CUDA;

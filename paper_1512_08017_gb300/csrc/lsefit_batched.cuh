@@ -58,11 +58,16 @@ struct BParams {
 };
 
 // ---------------------------------------------------------------------------
-// preparation launch: map constants of every series (one per thread)
+// preparation launch: clears the queue counters and split-series tickets, and
+// computes the map constants of every series (one per thread).  Clearing here
+// means the workspace needs no initialization and may be shared by plans of
+// different layouts.
 // ---------------------------------------------------------------------------
 template <bool FP32MAP>
 __global__ void batched_prep_kernel(BParams p) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < 3) p.counters[s] = 0u;
+    if (s < p.n_block_tasks) p.tickets[s] = 0u;
     if (s >= p.num_series) return;
     double c, sc;
     const bool ok = map_constants(p.interval ? p.interval + 2 * s : nullptr, FP32MAP, c, sc);

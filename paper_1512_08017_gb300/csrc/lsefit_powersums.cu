@@ -34,6 +34,17 @@ struct PSParams {
     int32_t* fit_status;    // [m-m_lo+1]
 };
 
+// The fused solves of lsefit_fit, kept out of line so that their FP64
+// register demand does not reshape the streaming loop of the kernel.
+template <int M>
+__device__ __noinline__ void ps_solve_degrees(const PSParams& p, const double* tot, double c, double s,
+                                              bool map_ok, int lane) {
+    const int d = p.m_lo + lane;
+    const int st = solve_hankel_rt<M>(d, tot, tot + 2 * M + 1, c, s, map_ok, p.eps,
+                                      p.Xt ? p.Xt + lane * (M + 1) : nullptr, p.X + lane * (M + 1), M + 1);
+    p.fit_status[lane] = st;
+}
+
 // Last block: fixed-order FP64 sum of the per-block partials, then the outputs.
 template <int M>
 __device__ void ps_finish(const PSParams& p, bool map_ok, double c, double s, double* comb) {
@@ -73,13 +84,7 @@ __device__ void ps_finish(const PSParams& p, bool map_ok, double c, double s, do
         // degree-M sums (S_0..S_2d, T_0..T_d), all lanes in step
         __syncthreads();
         const int lane = tid;
-        if (tid < 32 && lane <= M - p.m_lo) {
-            const int d = p.m_lo + lane;
-            const int st = solve_hankel_rt<M>(d, tot_s, tot_s + 2 * M + 1, c, s, map_ok, p.eps,
-                                              p.Xt ? p.Xt + lane * (M + 1) : nullptr, p.X + lane * (M + 1),
-                                              M + 1);
-            p.fit_status[lane] = st;
-        }
+        if (tid < 32 && lane <= M - p.m_lo) ps_solve_degrees<M>(p, tot_s, c, s, map_ok, lane);
     }
 }
 
