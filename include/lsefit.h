@@ -67,7 +67,8 @@ enum {
     LSEFIT_ERR_BAD_INTERVAL = 5,  /* per fit: interval not finite or hi <= lo */
     LSEFIT_ERR_WORKSPACE = 6,     /* host: workspace or plan buffer too small / misaligned */
     LSEFIT_ERR_CUDA = 7,          /* host: a CUDA runtime call or launch failed */
-    LSEFIT_ERR_UNSUPPORTED = 8    /* host: dtype/accum combination not provided */
+    LSEFIT_ERR_UNSUPPORTED = 8,   /* host: dtype/accum combination not provided */
+    LSEFIT_ERR_SCRATCH_LIMIT = 9  /* host: request exceeds the static scratch of lsefit_fit_noalloc */
 };
 
 /* Storage type of x and y. */
@@ -170,6 +171,37 @@ int lsefit_solve(const double* sums, int64_t count, int m_sums, int m, int accum
 int lsefit_fit(const void* x, const void* y, int64_t n, int dtype, int m, int m_lo, int accum,
                const double* interval, double* X, double* Xt, double* sums, double* map,
                int32_t* status, void* workspace, size_t workspace_bytes, lsefit_stream_t stream);
+
+/*
+ * lsefit_fit_noalloc -- lsefit_fit for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a deployment variant.
+ *
+ * Who needs it: a service that runs under a fixed device-memory budget and
+ * forbids allocation after start-up, or a plugin host that hands its
+ * plugins only their input and output buffers and offers no allocator.
+ * Such callers pass inputs and outputs only; the reduction's scratch (one
+ * ticket word and the per-block FP64 partials) lives in a static device
+ * array inside the library.
+ *  - Limit: the array has lsefit_fit_noalloc_scratch_bytes() = 819,456
+ *    bytes, enough for every degree up to LSEFIT_MAX_DEGREE and the largest
+ *    grid the library launches.  Every GPU that loads the library holds it
+ *    until the process exits.  A request that would need more returns
+ *    LSEFIT_ERR_SCRATCH_LIMIT (it cannot happen with valid degrees).
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current) and caches it; make that first call before any
+ *    stream capture.
+ *  - All calls share the one array.  Calls that overlap on the GPU (on
+ *    different streams, or from different threads) race on it; serialise
+ *    them.  The call clears the ticket word before its launch; the rest of
+ *    the array keeps the previous call's contents and needs no clearing.
+ *  - It allocates nothing: no cudaMalloc, cudaFree or allocating library
+ *    routine; it issues one 256-byte cudaMemsetAsync and the fit's launch.
+ *  Arguments, outputs and errors as for lsefit_fit, without the workspace.
+ */
+size_t lsefit_fit_noalloc_scratch_bytes(void);
+int lsefit_fit_noalloc(const void* x, const void* y, int64_t n, int dtype, int m, int m_lo, int accum,
+                       const double* interval, double* X, double* Xt, double* sums, double* map,
+                       int32_t* status, lsefit_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Batched ragged series (one persistent launch)

@@ -51,6 +51,7 @@ extern "C" const char* lsefit_status_string(int code) {
         case LSEFIT_ERR_WORKSPACE: return "workspace too small or misaligned";
         case LSEFIT_ERR_CUDA: return "CUDA error";
         case LSEFIT_ERR_UNSUPPORTED: return "unsupported dtype/accumulation";
+        case LSEFIT_ERR_SCRATCH_LIMIT: return "request exceeds the static scratch of lsefit_fit_noalloc";
         default: return "unknown status";
     }
 }

@@ -9,6 +9,8 @@
 // and stores them as per-block partials; the last block to finish (ticket
 // counter, no waiting) adds the partials in FP64 in a fixed order and writes
 // S_0..S_2m, T_0..T_m.  The result depends only on n and the launch shape.
+#include <mutex>
+
 #include "lsefit_device.cuh"
 #include "lsefit_host.h"
 
@@ -274,4 +276,65 @@ extern "C" int lsefit_fit(const void* x, const void* y, int64_t n, int dtype, in
     if (X == nullptr || status == nullptr) return LSEFIT_ERR_INVALID_ARG;
     return launch_powersums(x, y, n, dtype, m, accum, interval, sums, map, nullptr, workspace, workspace_bytes,
                             stream, m_lo, X, Xt, status);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free single-series fit.
+//
+// Some callers cannot allocate device memory at the time they fit: a service
+// that runs under a fixed device-memory budget and forbids allocation after
+// start-up, or a plugin host that hands its plugins only input and output
+// buffers and offers no allocator.  For them lsefit_fit_noalloc keeps the
+// reduction's scratch (the ticket word and the per-block FP64 partials) in the
+// file-scope array below instead of a caller workspace.  The array is sized
+// for the largest degree and grid, so every call of lsefit_fit fits in it.
+// Every GPU that loads the library holds it until the process exits.
+// ---------------------------------------------------------------------------
+namespace lsefit {
+
+constexpr size_t kNoallocScratchBytes = 819456;  // kAlign + kMaxGrid * (3*8+1) * 8
+static_assert(kNoallocScratchBytes >= kAlign + (size_t)kMaxGrid * (3 * LSEFIT_MAX_DEGREE + 1) * sizeof(double),
+              "allocation-free scratch must hold the partials of the largest degree and grid");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+// Device address of g_noalloc_scratch on the current device.  In host code the
+// symbol names a host-side stand-in, not device memory, so the address is
+// looked up once per device (with that device current) and cached.
+static int noalloc_scratch(void** out) {
+    static std::mutex mu;
+    static void* addr[256] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+        (void)cudaGetLastError();
+        return LSEFIT_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (addr[dev] == nullptr) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+            (void)cudaGetLastError();
+            return LSEFIT_ERR_CUDA;
+        }
+        addr[dev] = p;
+    }
+    *out = addr[dev];
+    return LSEFIT_OK;
+}
+
+}  // namespace lsefit
+
+extern "C" size_t lsefit_fit_noalloc_scratch_bytes(void) { return kNoallocScratchBytes; }
+
+extern "C" int lsefit_fit_noalloc(const void* x, const void* y, int64_t n, int dtype, int m, int m_lo,
+                                  int accum, const double* interval, double* X, double* Xt, double* sums,
+                                  double* map, int32_t* status, lsefit_stream_t stream) {
+    if (m < 1 || m > LSEFIT_MAX_DEGREE) return LSEFIT_ERR_INVALID_ARG;
+    if (lsefit_powersums_workspace_size(m) > kNoallocScratchBytes) return LSEFIT_ERR_SCRATCH_LIMIT;
+    void* ws = nullptr;
+    const int rc = noalloc_scratch(&ws);
+    if (rc != LSEFIT_OK) return rc;
+    // the ticket word must start at zero (each call also leaves it zeroed)
+    if (cudaMemsetAsync(ws, 0, kAlign, (cudaStream_t)stream) != cudaSuccess) return LSEFIT_ERR_CUDA;
+    return lsefit_fit(x, y, n, dtype, m, m_lo, accum, interval, X, Xt, sums, map, status, ws,
+                      kNoallocScratchBytes, stream);
 }

@@ -32,6 +32,7 @@ ERR_BAD_INTERVAL = 5
 ERR_WORKSPACE = 6
 ERR_CUDA = 7
 ERR_UNSUPPORTED = 8
+ERR_SCRATCH_LIMIT = 9
 
 F64, F32, BF16 = 0, 1, 2
 ACCUM = {"naive": 0, "comp": 1, "f64": 2}
@@ -84,6 +85,8 @@ SIGNATURES = {
     "lsefit_powersums": (_INT, [_VP, _VP, _I64, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "lsefit_solve": (_INT, [_VP, _I64, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP]),
     "lsefit_fit": (_INT, [_VP, _VP, _I64, _INT, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "lsefit_fit_noalloc_scratch_bytes": (_SZ, []),
+    "lsefit_fit_noalloc": (_INT, [_VP, _VP, _I64, _INT, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "lsefit_plan_build": (_INT, [_VP, _I64, _INT, _VP, _INT, _VP, _VP, _I64, _VP, _I64]),
     "lsefit_batched_workspace_size": (_SZ, [_VP]),
     "lsefit_fit_batched": (_INT, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
