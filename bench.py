@@ -51,6 +51,8 @@ def parse_args(argv=None):
     p.add_argument("--n", type=int, default=1 << 28, help="points of the single_large series")
     p.add_argument("--series", type=int, default=65536, help="series of the ragged_batch workload")
     p.add_argument("--no-plain", action="store_true", help="skip the plain per-series comparison")
+    p.add_argument("--tuning", default=None,
+                   help="batched schedule as JSON (e.g. '{\"warp_max_len\": 1048576}'); default: autotune")
     p.add_argument("--accum", default="comp", choices=["comp", "naive", "f64"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -392,10 +394,13 @@ def run_ragged_batch(args, dist: Dist):
     deg = torch.from_numpy(b["degree"]).to(dev)
     iv = torch.from_numpy(b["interval"]).to(dev)
     t_tune = time.perf_counter()
-    tuning, tried = autotune.tune_batched(x, y, off, deg, iv, m_max=m_max, accum=args.accum)
+    if args.tuning:
+        tuning, tried = json.loads(args.tuning), []
+    else:
+        tuning, tried = autotune.tune_batched(x, y, off, deg, iv, m_max=m_max, accum=args.accum)
     t_tune = time.perf_counter() - t_tune
     t_plan = time.perf_counter()
-    plan = L.BatchPlan(b["offsets"], m_max, tuning=tuning, device=dev)
+    plan = L.BatchPlan(b["offsets"], m_max, tuning=tuning, device=dev, degree=b["degree"])
     t_plan = time.perf_counter() - t_plan
     out = {"X": torch.empty(S, m_max + 1, dtype=torch.float64, device=dev),
            "status": torch.empty(S, dtype=torch.int32, device=dev)}
@@ -531,7 +536,12 @@ def run_diff_batch(args, dist: Dist):
     deg = torch.full((S,), m, dtype=torch.int32, device=dev)
     iv = torch.tensor([[-1.0, 1.0]] * S, dtype=torch.float64, device=dev)
     w = torch.from_numpy(d["w"]).to(dev)
-    plan = L.BatchPlan(offsets, m, tuning={"warp_max_len": 1024, "chunk_len": 4096}, device=dev)
+    from paper_1512_08017_gb300 import autotune
+    if args.tuning:
+        tuning = json.loads(args.tuning)
+    else:
+        tuning, _ = autotune.tune_batched(x, y, off, deg, iv, m_max=m, accum=args.accum)
+    plan = L.BatchPlan(offsets, m, tuning=tuning, device=dev)
     fwd_out = {"X": torch.empty(S, m + 1, dtype=torch.float64, device=dev),
                "Xt": torch.empty(S, m + 1, dtype=torch.float64, device=dev),
                "sums": torch.empty(S, 3 * m + 2, dtype=torch.float64, device=dev),

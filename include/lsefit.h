@@ -226,8 +226,8 @@ typedef struct lsefit_tuning {
     int32_t chunk_len;        /* longer series are cut into chunks of about this many points,
                                  each reduced by one block; a series with one chunk is finished
                                  by its block, others by the block that completes them last */
-    int32_t block_threads;    /* 128, 256 or 512 */
-    int32_t blocks_per_sm;    /* persistent blocks per SM (0 = occupancy maximum) */
+    int32_t block_threads;    /* reserved (the batched kernel runs 512 threads per block) */
+    int32_t blocks_per_sm;    /* reserved (one persistent block per SM) */
     int32_t reserved[4];
 } lsefit_tuning;
 
@@ -238,32 +238,38 @@ typedef struct lsefit_plan {
     int64_t num_series;
     int64_t total_points;
     int32_t n_block_tasks;    /* entries of block_tasks (4 int32 each) */
-    int32_t n_warp_tasks;     /* entries of warp_tasks (1 int32 each) */
+    int32_t n_warp_tasks;     /* entries of warp_tasks (4 int32 each) */
     int32_t n_split_series;   /* series cut into more than one chunk */
     int32_t m_max;
     lsefit_tuning tuning;     /* resolved values */
     int32_t grid;             /* persistent grid size */
     int32_t num_sms;
     const int32_t* block_tasks;  /* device int32[n_block_tasks][4]: series, chunk, nchunks, first task */
-    const int32_t* warp_tasks;   /* device int32[n_warp_tasks]: series ids, longest first */
+    const int32_t* warp_tasks;   /* device int32[n_warp_tasks][4]: series, first point (low and
+                                    high 32 bits), length; longest first */
 } lsefit_plan;
 
 /*
  * lsefit_plan_build -- split a batch layout into block tasks (series longer
  * than tuning.warp_max_len, cut into chunks) and warp tasks (the shorter
- * series), longest first.  Host only; no GPU needed.
+ * series).  Block tasks are ordered longest first; warp tasks longest first
+ * too, grouped by degree (lowest first) when degrees are given, so that the
+ * warps working side by side run the same code.  Host only; no GPU needed.
  *  offsets_host  host int64[num_series+1] (nondecreasing, offsets[0] = 0).
+ *  degree_host   host int32[num_series] or NULL (the same degrees the fits
+ *                will use; only the order of the tasks depends on them).
  *  tuning        host, or NULL for defaults.
  *  num_sms       SM count of the target device (> 0).
  *  plan          host, written.
  *  block_tasks_host / warp_tasks_host  host buffers of capacity
- *                block_cap (entries of 4 int32) and warp_cap entries, written.
+ *                block_cap and warp_cap entries of 4 int32 each, written.
+ *                A warp task's length must fit an int32 (warp_max_len <= 2^31-1).
  *                Pass NULL with zero capacity to query: plan->n_block_tasks
  *                and plan->n_warp_tasks are still set, and the call returns
  *                LSEFIT_ERR_WORKSPACE.
  */
-int lsefit_plan_build(const int64_t* offsets_host, int64_t num_series, int m_max,
-                      const lsefit_tuning* tuning, int num_sms, lsefit_plan* plan,
+int lsefit_plan_build(const int64_t* offsets_host, const int32_t* degree_host, int64_t num_series,
+                      int m_max, const lsefit_tuning* tuning, int num_sms, lsefit_plan* plan,
                       int32_t* block_tasks_host, int64_t block_cap,
                       int32_t* warp_tasks_host, int64_t warp_cap);
 
@@ -293,6 +299,55 @@ size_t lsefit_batched_workspace_size(const lsefit_plan* plan);
 int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* plan, double* X,
                        double* Xt, double* sums, double* map, int32_t* status,
                        void* workspace, size_t workspace_bytes, lsefit_stream_t stream);
+
+/* Bytes of workspace lsefit_range needs for `plan`. */
+size_t lsefit_range_workspace_size(const lsefit_plan* plan);
+
+/*
+ * lsefit_range -- interval prepass: writes, per series, the smallest and
+ * largest abscissa, for fits whose caller does not know the interval of the
+ * affine map (not in the paper; the map keeps the Hankel system of
+ * Section II well-conditioned).  Exact (minimum and maximum do not depend on
+ * the order of evaluation); NaN points are ignored.  Reads x once (the
+ * prepass costs the bytes of x on top of the fit).
+ *  batch     as for lsefit_fit_batched (y, degree and interval unused).
+ *  plan      from lsefit_plan_build for the layout, device task arrays set.
+ *  interval  device double[num_series][2], written {lo, hi}; {NaN, NaN} for
+ *            a series without a non-NaN point (its fit then reports
+ *            LSEFIT_ERR_BAD_INTERVAL).
+ *  workspace device, >= lsefit_range_workspace_size(plan), 256-byte aligned,
+ *            zero-filled before first use (each call leaves it zeroed).
+ */
+int lsefit_range(const lsefit_batch* batch, const lsefit_plan* plan, double* interval,
+                 void* workspace, size_t workspace_bytes, lsefit_stream_t stream);
+
+/* Bytes of workspace lsefit_residuals needs for `plan`. */
+size_t lsefit_residuals_workspace_size(const lsefit_plan* plan);
+
+/*
+ * lsefit_residuals -- fitted values and residual errors of a batched fit
+ * (Section III judges a fit by its residuals e_i = y_i - f(x_i) and their sum
+ * of squares, Table V).  One more pass over the points:
+ *   SSE_s = sum_i r_i^2,  (V^T r)_{s,k} = sum_i t_i^k r_i  (k = 0..m),
+ * with r_i = y_i - f(t_i), f(t) = sum_k Xt_k t^k by Horner's rule on the
+ * mapped abscissae t_i = s (x_i - c).  V^T r vanishes at the least-squares
+ * solution (the normal equations of Section II), so it measures how well a
+ * fit satisfies them.  FP32 per point, compensated double-float sums, FP64
+ * chunk combine; FP64 throughout for FP64 data.
+ *  batch     as for lsefit_fit_batched (interval unused: the map is `map`).
+ *  plan      the layout's plan, device task arrays set.
+ *  Xt        device double[num_series][m_max+1] (from lsefit_fit_batched).
+ *  map       device double[num_series][2] {c, s} or NULL (identity).
+ *  r         device array like y or NULL: per-point residuals (FP32 for
+ *            F32/BF16 data, FP64 for F64 data).
+ *  sse       device double[num_series]: NaN for a series whose fit failed.
+ *  vtr       device double[num_series][m_max+1] or NULL.
+ *  workspace device, >= lsefit_residuals_workspace_size(plan), 256-byte
+ *            aligned; no initialization needed.
+ */
+int lsefit_residuals(const lsefit_batch* batch, const lsefit_plan* plan, const double* Xt,
+                     const double* map, void* r, double* sse, double* vtr, void* workspace,
+                     size_t workspace_bytes, lsefit_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Adjoint

@@ -22,12 +22,10 @@ import torch
 from . import lsefit as L
 
 DEFAULT_CANDIDATES = [
-    {"warp_max_len": wm, "chunk_len": ch, "blocks_per_sm": bps}
-    for wm in (1024, 8192, 65536)
-    for ch in (32768, 131072)
-    for bps in (0,)
-] + [{"warp_max_len": 256, "chunk_len": 16384, "blocks_per_sm": 0},
-     {"warp_max_len": 8192, "chunk_len": 65536, "blocks_per_sm": 1}]
+    {"warp_max_len": wm, "chunk_len": ch}
+    for wm in (4096, 65536, 1 << 20)
+    for ch in (65536, 262144)
+] + [{"warp_max_len": 1024, "chunk_len": 16384}]
 
 _lock = threading.Lock()
 
@@ -109,7 +107,7 @@ def tune_batched(x, y, offsets, degree, interval=None, m_max=None, accum="comp",
             return dict(cache[key]["tuning"]), []
     results = []
     for cand in candidates or DEFAULT_CANDIDATES:
-        plan = L.BatchPlan(off_host, m_max, tuning=cand, device=dev)
+        plan = L.BatchPlan(off_host, m_max, tuning=cand, device=dev, degree=degree)
         ms = time_plan(x, y, offsets_d, degree_d, interval_d, m_max, accum, plan, reps=reps)
         results.append((dict(cand), ms))
         if verbose:

@@ -40,7 +40,7 @@ struct BwParams {
     const int32_t* status;  // [S]
     const int4* block_tasks;
     int n_block_tasks;
-    const int32_t* warp_tasks;
+    const int4* warp_tasks;  // {series, first point (low, high), length}
     int n_warp_tasks;
     unsigned* counters;     // [0] block queue, [1] warp queue, [2] exited blocks
 };
@@ -188,8 +188,8 @@ __device__ __forceinline__ void grad_range_f32(const BwParams& p, int64_t b, int
     const uint4* yv = reinterpret_cast<const uint4*>(static_cast<const char*>(p.y) + (b + head) * ES);
     float4* dxv = reinterpret_cast<float4*>(dx + b + head);
     float4* dyv = reinterpret_cast<float4*>(dy + b + head);
-    for (int64_t v = rank; v < nvec; v += nthreads) {
-        const uint4 xr = ld_stream16(xv + v), yr = ld_stream16(yv + v);
+    // one 16-byte vector of x and y -> 4 gradients of each
+    auto grad_vec = [&](uint4 xr, uint4 yr, float4& ox, float4& oy) {
         u64 ta = mul2(sub2(pk2(__uint_as_float(xr.x), __uint_as_float(xr.y)), c2), s2);
         u64 tb = mul2(sub2(pk2(__uint_as_float(xr.z), __uint_as_float(xr.w)), c2), s2);
         u64 ya = pk2(__uint_as_float(yr.x), __uint_as_float(yr.y));
@@ -197,11 +197,31 @@ __device__ __forceinline__ void grad_range_f32(const BwParams& p, int64_t b, int
         u64 gxa, gya, gxb, gyb;
         grad_pair<M>(lam, xt, ta, ya, s2, gxa, gya);
         grad_pair<M>(lam, xt, tb, yb, s2, gxb, gyb);
-        float4 ox, oy;
         up2(gxa, ox.x, ox.y);
         up2(gxb, ox.z, ox.w);
         up2(gya, oy.x, oy.y);
         up2(gyb, oy.z, oy.w);
+    };
+    constexpr int U = 4;  // vectors in flight per thread
+    int64_t v = rank;
+    for (; v + (U - 1) * nthreads < nvec; v += U * nthreads) {
+        uint4 xr[U], yr[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            xr[u] = ld_stream16(xv + v + u * nthreads);
+            yr[u] = ld_stream16(yv + v + u * nthreads);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            float4 ox, oy;
+            grad_vec(xr[u], yr[u], ox, oy);
+            __stcs(dxv + v + u * nthreads, ox);
+            __stcs(dyv + v + u * nthreads, oy);
+        }
+    }
+    for (; v < nvec; v += nthreads) {
+        float4 ox, oy;
+        grad_vec(ld_stream16(xv + v), ld_stream16(yv + v), ox, oy);
         __stcs(dxv + v, ox);
         __stcs(dyv + v, oy);
     }
@@ -320,7 +340,7 @@ __global__ void __launch_bounds__(kBwBlock) grad_kernel(BwParams p) {
         if (lane == 0) t = (int)atomicAdd(&p.counters[1], 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= p.n_warp_tasks) break;
-        const int64_t s = p.warp_tasks[t];
+        const int64_t s = p.warp_tasks[t].x;
         grad_dispatch<DT>(p, s, p.offsets[s], p.offsets[s + 1], lane, 32);
     }
     __syncthreads();
@@ -404,7 +424,7 @@ extern "C" int lsefit_backward(const lsefit_batch* batch, const lsefit_plan* pla
     p.status = status;
     p.block_tasks = reinterpret_cast<const int4*>(plan->block_tasks);
     p.n_block_tasks = plan->n_block_tasks;
-    p.warp_tasks = plan->warp_tasks;
+    p.warp_tasks = reinterpret_cast<const int4*>(plan->warp_tasks);
     p.n_warp_tasks = plan->n_warp_tasks;
     p.counters = reinterpret_cast<unsigned*>(ws);
     auto gk = b.dtype == LSEFIT_F64 ? grad_kernel<LSEFIT_F64>

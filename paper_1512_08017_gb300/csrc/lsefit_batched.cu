@@ -32,7 +32,7 @@ static void resolve_tuning(const lsefit_tuning* in, lsefit_tuning* out) {
     if (t.chunk_len <= 0) t.chunk_len = kDefaultChunkLen;
     if (t.chunk_len < 1024) t.chunk_len = 1024;
     t.block_threads = kBBlock;
-    if (t.blocks_per_sm < 0) t.blocks_per_sm = 0;
+    t.blocks_per_sm = 1;
     *out = t;
 }
 
@@ -40,8 +40,8 @@ static void resolve_tuning(const lsefit_tuning* in, lsefit_tuning* out) {
 
 using namespace lsefit;
 
-extern "C" int lsefit_plan_build(const int64_t* offsets, int64_t num_series, int m_max,
-                                 const lsefit_tuning* tuning, int num_sms, lsefit_plan* plan,
+extern "C" int lsefit_plan_build(const int64_t* offsets, const int32_t* degree, int64_t num_series,
+                                 int m_max, const lsefit_tuning* tuning, int num_sms, lsefit_plan* plan,
                                  int32_t* block_tasks, int64_t block_cap, int32_t* warp_tasks,
                                  int64_t warp_cap) {
     if (plan == nullptr || offsets == nullptr || num_series < 0 || num_series >= (int64_t(1) << 31) ||
@@ -76,13 +76,23 @@ extern "C" int lsefit_plan_build(const int64_t* offsets, int64_t num_series, int
     plan->m_max = m_max;
     plan->num_sms = num_sms;
     plan->grid = 0;
+    if (wmax > 0x7fffffffll) return LSEFIT_ERR_INVALID_ARG;  // a warp task's length is an int32
     if (block_cap < nbt || warp_cap < (int64_t)shorts.size() || (nbt > 0 && block_tasks == nullptr) ||
         (!shorts.empty() && warp_tasks == nullptr))
         return LSEFIT_ERR_WORKSPACE;
     auto len_of = [&](int32_t s) { return offsets[s + 1] - offsets[s]; };
     auto longer = [&](int32_t a, int32_t b) { return len_of(a) > len_of(b); };
     std::stable_sort(longs.begin(), longs.end(), longer);
-    std::stable_sort(shorts.begin(), shorts.end(), longer);
+    if (degree != nullptr) {
+        // group the warp tasks by degree (the warps of an SM then run the same
+        // code at the same time), longest first within a degree
+        auto by_degree = [&](int32_t a, int32_t b) {
+            return degree[a] != degree[b] ? degree[a] < degree[b] : len_of(a) > len_of(b);
+        };
+        std::stable_sort(shorts.begin(), shorts.end(), by_degree);
+    } else {
+        std::stable_sort(shorts.begin(), shorts.end(), longer);
+    }
     int64_t t = 0;
     for (int32_t s : longs) {
         const int64_t nch = (len_of(s) + ch - 1) / ch;
@@ -94,7 +104,14 @@ extern "C" int lsefit_plan_build(const int64_t* offsets, int64_t num_series, int
             block_tasks[4 * t + 3] = (int32_t)first;
         }
     }
-    std::copy(shorts.begin(), shorts.end(), warp_tasks);
+    for (size_t i = 0; i < shorts.size(); ++i) {
+        const int32_t sid = shorts[i];
+        const uint64_t b = (uint64_t)offsets[sid];
+        warp_tasks[4 * i + 0] = sid;
+        warp_tasks[4 * i + 1] = (int32_t)(uint32_t)(b & 0xffffffffu);
+        warp_tasks[4 * i + 2] = (int32_t)(uint32_t)(b >> 32);
+        warp_tasks[4 * i + 3] = (int32_t)len_of(sid);
+    }
     return LSEFIT_OK;
 }
 
@@ -108,10 +125,18 @@ static size_t ws_map_off(const lsefit_plan* plan) {
     return ws_partials_off(plan) +
            align_up((size_t)plan->n_block_tasks * (size_t)(3 * plan->m_max + 1) * sizeof(double), kAlign);
 }
+// queues of finished series: one per warp of a grid of one block per SM
+static size_t ws_pend_off(const lsefit_plan* plan) {
+    return ws_map_off(plan) + align_up((size_t)plan->num_series * 16, kAlign);
+}
+static size_t ws_pend_bytes(const lsefit_plan* plan) {
+    const int nmax = plan->m_max <= 5 ? 5 : 8;
+    return align_up((size_t)plan->num_sms * kBWarps * pend_warp_bytes(nmax), kAlign);
+}
 
 extern "C" size_t lsefit_batched_workspace_size(const lsefit_plan* plan) {
-    if (plan == nullptr || plan->n_block_tasks < 0 || plan->num_series < 0) return 0;
-    return ws_map_off(plan) + align_up((size_t)plan->num_series * 16, kAlign);
+    if (plan == nullptr || plan->n_block_tasks < 0 || plan->num_series < 0 || plan->num_sms <= 0) return 0;
+    return ws_pend_off(plan) + ws_pend_bytes(plan);
 }
 
 extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* plan, double* X,
@@ -146,8 +171,9 @@ extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* 
     p.m_max = b.m_max;
     p.block_tasks = reinterpret_cast<const int4*>(plan->block_tasks);
     p.n_block_tasks = plan->n_block_tasks;
-    p.warp_tasks = plan->warp_tasks;
+    p.warp_tasks = reinterpret_cast<const int4*>(plan->warp_tasks);
     p.n_warp_tasks = plan->n_warp_tasks;
+    p.total_points = plan->total_points;
     p.X = X;
     p.Xt = Xt;
     p.sums = sums;
@@ -159,6 +185,7 @@ extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* 
     p.tickets = reinterpret_cast<unsigned*>(ws + ws_tickets_off());
     p.partials = reinterpret_cast<double*>(ws + ws_partials_off(plan));
     p.mapc = reinterpret_cast<double2*>(ws + ws_map_off(plan));
+    p.pend = reinterpret_cast<unsigned char*>(ws + ws_pend_off(plan));
 
     const int nmax = b.m_max <= 5 ? 5 : 8;
     batched_kernel_t k = pick_batched(b.dtype, b.accum, nmax);
@@ -178,10 +205,10 @@ extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* 
             configured.push_back(key);
         }
     }
-    int bps = plan->tuning.blocks_per_sm;
-    const int occ = occupancy_blocks(reinterpret_cast<const void*>(k), kBBlock, smem);
-    if (bps <= 0 || bps > occ) bps = occ;
-    int64_t grid = (int64_t)sms * bps;
+    // one block per SM: the warp rings take most of its shared memory; the
+    // workspace holds the queues of exactly that many warps
+    if (sms > plan->num_sms) return LSEFIT_ERR_INVALID_ARG;  // plan built for a smaller device
+    int64_t grid = (int64_t)sms;
     const int64_t useful = (int64_t)plan->n_block_tasks + (plan->n_warp_tasks + kBWarps - 1) / kBWarps;
     if (useful < grid) grid = useful;
     if (grid < 1) grid = 1;

@@ -9,8 +9,15 @@
 //     adds the partials in chunk order (no block ever waits for another);
 //   * warp tasks: the shorter series, longest first; one warp reduces one
 //     series.
-// Persistent blocks take block tasks from an atomic queue until it is
-// empty, then each warp takes warp tasks from a second queue.
+// Persistent blocks (one per SM: the warp rings take most of its shared
+// memory) take block tasks from an atomic queue until it is
+// empty.  Then every warp works through warp tasks in a fixed snake order
+// (round r gives warp w task r*W + w, or r*W + W-1-w on odd rounds, W warps
+// in the grid): with the tasks sorted longest first this balances the warps
+// and lets each one prefetch its next tasks' records.  A warp streams its
+// series through a ring of shared-memory stages filled by cp.async copies
+// that run ahead across task boundaries, so the bytes in flight do not
+// depend on registers or on the length of the current series.
 //
 // FP64 placement.  GB300 runs FP64 at 1/64 of the FP32 rate, and a warp
 // instruction costs the same whether one lane or 32 use it.  So no FP64
@@ -28,9 +35,9 @@
 
 namespace lsefit {
 
-constexpr int kBBlock = 256;
+constexpr int kBBlock = 512;
 constexpr int kBWarps = kBBlock / 32;
-constexpr int kDefaultWarpMaxLen = 8192;
+constexpr int kDefaultWarpMaxLen = 65536;
 constexpr int kDefaultChunkLen = 65536;
 
 struct BParams {
@@ -43,8 +50,9 @@ struct BParams {
     int m_max;
     const int4* block_tasks;
     int n_block_tasks;
-    const int32_t* warp_tasks;
+    const int4* warp_tasks;   // {series, first point (low, high 32 bits), length}
     int n_warp_tasks;
+    int64_t total_points;
     double* X;
     double* Xt;
     double* sums;
@@ -55,6 +63,7 @@ struct BParams {
     unsigned* tickets;     // [n_block_tasks], slot of a split series = its first task
     unsigned* counters;    // [0] block queue, [1] warp queue, [2] exited blocks
     double2* mapc;         // [num_series]: FP32 paths {float2(c, s), unused}; FP64 {c, s}
+    unsigned char* pend;   // [grid * kBWarps] queues of finished series
 };
 
 // ---------------------------------------------------------------------------
@@ -112,20 +121,21 @@ __device__ __forceinline__ bool load_map_f64(const BParams& p, int64_t s, double
 template <int NMAX>
 struct PendLayout {
     static constexpr int kStride = 3 * NMAX + 2;
-    static constexpr int kBytes = 32 * kStride * 8 + 32 * 4 * 2 + 16;
+    // per warp, in the workspace: rows [32][kStride] words, then sid[32], meta[32]
+    static constexpr size_t kWarpBytes = (size_t)32 * kStride * 8 + 32 * 4 * 2;
 };
 
 template <int NMAX>
 struct Pend {
-    unsigned long long* row;  // [32][kStride] 8-byte words
-    int* sid;                 // [32] series id
-    int* meta;                // [32] degree
-    int* count;               // [1]
-    __device__ __forceinline__ void bind(unsigned char* base) {
+    unsigned long long* row;  // [32][kStride] 8-byte words (global workspace)
+    int* sid;                 // [32] series id (global workspace)
+    int* meta;                // [32] degree (global workspace)
+    int* count;               // [1] (shared memory)
+    __device__ __forceinline__ void bind(unsigned char* base, int* cnt) {
         row = reinterpret_cast<unsigned long long*>(base);
         sid = reinterpret_cast<int*>(base + 32 * PendLayout<NMAX>::kStride * 8);
         meta = sid + 32;
-        count = meta + 32;
+        count = cnt;
     }
 };
 
@@ -139,56 +149,241 @@ __device__ __forceinline__ dflt bits_df(unsigned long long w) {
     return v;
 }
 
-// red (block reduction scratch, kBWarps x kBBlock values of 8 bytes), blk, comb, queues
-constexpr size_t kRedBytes = (size_t)kBWarps * kBBlock * 8;
+// ---------------------------------------------------------------------------
+// Warp stage rings (phase 2).  Stage boundaries lie on a fixed grid of
+// kStageBytes in the concatenated arrays, so every stage is a slice of one
+// aligned block and all but the first and last stage of a series are full.
+// ---------------------------------------------------------------------------
+constexpr int kRing = 3;                         // stages per warp ring
+constexpr int kStageBytes = 2048;                // bytes of x (and of y) per stage
+constexpr int kStageVecs = kStageBytes / 16;     // 16-byte vectors per stage (4 per lane)
+constexpr int kFoldStages = 2;                   // compensated batch = this many stages
+constexpr int kBlockUnroll = 2;                  // vectors in flight per thread in block tasks
 
-__host__ __device__ constexpr size_t batched_smem_bytes(int nmax) {
-    return kRedBytes + 32 * 8 /* blk */ + 32 * 8 /* comb */ +
-           (size_t)kBWarps * (32 * (3 * nmax + 2) * 8 + 32 * 4 * 2 + 16);
+struct __align__(16) StageRec {
+    long long r0;   // first point of the stage
+    int n;          // points in the stage
+    int s;          // series
+    int flags;      // 1: first stage of the series, 2: last stage
+    int deg;        // degree of the series
+    double2 map;    // prepared map constants (raw 16 bytes, see batched_prep_kernel)
+};
+
+constexpr int kRingWarpBytes = 2 * kRing * kStageBytes + kRing * (int)sizeof(StageRec);
+
+// Shared memory: [block-reduction scratch | warp rings] (phases 1 and 2 never
+// overlap), blk, comb and the queue counts; the queues of finished series
+// live in the workspace (written and read once per series).
+constexpr size_t kRedBytes = (size_t)kBWarps * kBBlock * 8;
+constexpr size_t kRingsBytes = (size_t)kBWarps * kRingWarpBytes;
+constexpr size_t kScratchBytes = kRedBytes > kRingsBytes ? kRedBytes : kRingsBytes;
+
+__host__ __device__ constexpr size_t batched_smem_bytes(int /*nmax*/) {
+    return kScratchBytes + 32 * 8 /* blk */ + 32 * 8 /* comb */ + kBWarps * 4 /* queue counts */;
 }
 
-// The warp solves its queued series, one per lane, and empties the queue.
+__host__ __device__ constexpr size_t pend_warp_bytes(int nmax) {
+    return (size_t)32 * (3 * nmax + 2) * 8 + 32 * 4 * 2;
+}
+
+struct Ring {
+    unsigned char* x;  // [kRing][kStageBytes]
+    unsigned char* y;  // [kRing][kStageBytes]
+    StageRec* rec;     // [kRing]
+    __device__ __forceinline__ void bind(unsigned char* base) {
+        x = base;
+        y = base + kRing * kStageBytes;
+        rec = reinterpret_cast<StageRec*>(base + 2 * kRing * kStageBytes);
+    }
+};
+
+// Producer cursor of a warp (registers, identical in all lanes).  Two task
+// records are prefetched ahead: `b` has its degree and map loaded too, `a`
+// only its record, so no load on the issue path waits for another.
+struct Cursor {
+    int round, wid, nw;
+    bool have;
+    int s, deg;
+    long long pos, end;
+    double2 map;
+    bool first;
+    bool bv;
+    int4 brec;
+    int bdeg;
+    double2 bmap;
+    bool av;
+    int4 arec;
+};
+
+__device__ __forceinline__ void cursor_fetch_record(Cursor& cu, const BParams& p) {
+    const long long t =
+        (long long)cu.round * cu.nw + ((cu.round & 1) ? (cu.nw - 1 - cu.wid) : cu.wid);
+    cu.round++;
+    cu.av = t < p.n_warp_tasks;
+    if (cu.av) cu.arec = p.warp_tasks[t];
+}
+
+// Make task b current, move a into b (loading its degree and map) and fetch a
+// new record into a.  Tasks of an invalid degree are marked and skipped.
+__device__ __forceinline__ void cursor_advance(Cursor& cu, const BParams& p) {
+    for (;;) {
+        cu.have = cu.bv;
+        if (cu.have) {
+            cu.s = cu.brec.x;
+            cu.pos = ((long long)(unsigned)cu.brec.z << 32) | (unsigned)cu.brec.y;
+            cu.end = cu.pos + cu.brec.w;
+            cu.deg = cu.bdeg;
+            cu.map = cu.bmap;
+            cu.first = true;
+        }
+        cu.bv = cu.av;
+        if (cu.bv) {
+            cu.brec = cu.arec;
+            cu.bdeg = p.degree[cu.arec.x];
+            cu.bmap = p.mapc[cu.arec.x];
+            cursor_fetch_record(cu, p);
+        }
+        if (!cu.have || (cu.deg >= 1 && cu.deg <= p.m_max)) return;
+        // not fitted at all: status and NaN row, no stages
+        if ((threadIdx.x & 31) == 0) {
+            const int64_t s = cu.s;
+            const int nc = p.m_max + 1;
+            const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+            for (int i = 0; i < nc; ++i) {
+                p.X[s * nc + i] = qnan;
+                if (p.Xt) p.Xt[s * nc + i] = qnan;
+            }
+            if (p.sums)
+                for (int k = 0; k < 3 * p.m_max + 2; ++k) p.sums[s * (3 * p.m_max + 2) + k] = qnan;
+            p.status[s] = LSEFIT_ERR_INVALID_ARG;
+        }
+    }
+}
+
+template <int ES>
+__device__ __forceinline__ void copy_elem(unsigned char* dst, const unsigned char* src) {
+    if (ES == 2) *reinterpret_cast<unsigned short*>(dst) = *reinterpret_cast<const unsigned short*>(src);
+    else if (ES == 4) *reinterpret_cast<unsigned*>(dst) = *reinterpret_cast<const unsigned*>(src);
+    else *reinterpret_cast<unsigned long long*>(dst) = *reinterpret_cast<const unsigned long long*>(src);
+}
+
+// Issue the next stage of the cursor's series into ring slot `slot` (all
+// lanes; one commit group per call).  Returns false when the warp has no
+// work left.
+template <int DT>
+__device__ __forceinline__ bool issue_stage(const BParams& p, Ring& R, int slot, Cursor& cu) {
+    if (!cu.have) return false;
+    constexpr int ES = Elem<DT>::kSize, PV = Elem<DT>::kPerVec, P = kStageBytes / ES;
+    const int lane = threadIdx.x & 31;
+    const long long r0 = cu.pos;
+    const long long r1 = min(cu.end, (r0 / P + 1) * P);
+    const long long g0 = r0 & ~(long long)(PV - 1);
+    const long long gend = (r1 + PV - 1) & ~(long long)(PV - 1);
+    const int nv = (int)((gend - g0) / PV);
+    unsigned char* xb = R.x + slot * kStageBytes;
+    unsigned char* yb = R.y + slot * kStageBytes;
+    const unsigned char* xg = static_cast<const unsigned char*>(p.x) + g0 * ES;
+    const unsigned char* yg = static_cast<const unsigned char*>(p.y) + g0 * ES;
+    if (gend <= p.total_points) {
+        for (int v = lane; v < nv; v += 32) {
+            cp_async16(xb + 16 * v, xg + 16 * v);
+            cp_async16(yb + 16 * v, yg + 16 * v);
+        }
+    } else for (int v = lane; v < nv; v += 32) {
+        if (g0 + (long long)(v + 1) * PV <= p.total_points) {
+            cp_async16(xb + 16 * v, xg + 16 * v);
+            cp_async16(yb + 16 * v, yg + 16 * v);
+        } else {
+            // the vector that crosses the end of the arrays: element by element
+            for (int u = 0; u < PV; ++u) {
+                if (g0 + (long long)v * PV + u < p.total_points) {
+                    copy_elem<ES>(xb + 16 * v + u * ES, xg + 16 * v + u * ES);
+                    copy_elem<ES>(yb + 16 * v + u * ES, yg + 16 * v + u * ES);
+                }
+            }
+        }
+    }
+    cp_async_commit();
+    if (lane == 0) {
+        StageRec& rc = R.rec[slot];
+        rc.r0 = r0;
+        rc.n = (int)(r1 - r0);
+        rc.s = cu.s;
+        rc.flags = (cu.first ? 1 : 0) | (r1 == cu.end ? 2 : 0);
+        rc.deg = cu.deg;
+        rc.map = cu.map;
+    }
+    cu.first = false;
+    cu.pos = r1;
+    if (r1 == cu.end) cursor_advance(cu, p);
+    return true;
+}
+
+// Wait until the oldest of `pending` stages has landed, then make every
+// lane's copies visible to the warp.
+__device__ __forceinline__ void ring_wait(int pending) {
+    static_assert(kRing == 3, "ring_wait covers up to three pending stages");
+    switch (pending) {
+        case 1: cp_async_wait<0>(); break;
+        case 2: cp_async_wait<1>(); break;
+        default: cp_async_wait<2>(); break;
+    }
+    __syncwarp();
+}
+
+// Solve one queued series (entry idx of warp ws's queue in this block), if
+// `active`.  Converts the entry's sums to FP64 in place.
+template <int NMAX, int ACC>
+__device__ __noinline__ void pend_solve_entry(const BParams& p, unsigned char* pend_block, int ws, int idx,
+                                              bool active) {
+    if (!active) return;
+    constexpr int W = PendLayout<NMAX>::kStride;
+    unsigned char* base = pend_block + (size_t)ws * PendLayout<NMAX>::kWarpBytes;
+    unsigned long long* row = reinterpret_cast<unsigned long long*>(base) + (size_t)idx * W;
+    const int* sid = reinterpret_cast<const int*>(base + 32 * W * 8);
+    const int m = sid[32 + idx];
+    const int64_t s = sid[idx];
+    const int ns = 3 * m + 2;
+    double* sm = reinterpret_cast<double*>(row);
+    sm[0] = (double)(long long)row[0];
+    if (ACC != LSEFIT_ACCUM_F64) {
+        for (int k = 1; k < ns; ++k) {
+            const dflt v = bits_df(row[k]);
+            sm[k] = f32_to_f64_int(v.hi) + f32_to_f64_int(v.lo);
+        }
+    }
+    double c, sc;
+    bool ok;
+    if (ACC == LSEFIT_ACCUM_F64) {
+        ok = load_map_f64(p, s, c, sc);
+    } else {
+        float cf, sf;
+        ok = load_map_f32(p, s, cf, sf);
+        c = f32_to_f64_int(cf);
+        sc = f32_to_f64_int(sf);
+    }
+    const int nc = p.m_max + 1;
+    const int st = solve_hankel_rt<NMAX>(m, sm, sm + 2 * m + 1, c, sc, ok, p.eps,
+                                         p.Xt ? p.Xt + s * nc : nullptr, p.X + s * nc, nc);
+    p.status[s] = st;
+    if (p.sums) {
+        const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+        const int stride = 3 * p.m_max + 2;
+        double* out = p.sums + s * stride;
+        for (int k = 0; k < stride; ++k) out[k] = k < ns ? (ok ? sm[k] : qnan) : 0.0;
+    }
+}
+
+// The warp solves its full queue (32 series), one per lane, and empties it.
 template <int NMAX, int ACC>
 __device__ __forceinline__ void pend_solve(const BParams& p, Pend<NMAX>& q) {
     __syncwarp();
     const int lane = threadIdx.x & 31;
     const int cnt = *q.count;
-    if (lane < cnt) {
-        constexpr int W = PendLayout<NMAX>::kStride;
-        unsigned long long* row = q.row + lane * W;
-        const int m = q.meta[lane];
-        const int64_t s = q.sid[lane];
-        const int ns = 3 * m + 2;
-        // convert this lane's row to doubles in place: S_0..S_2m, T_0..T_m
-        double* sm = reinterpret_cast<double*>(row);
-        sm[0] = (double)(long long)row[0];
-        for (int k = 1; k < ns; ++k) {
-            if (ACC != LSEFIT_ACCUM_F64) {
-                const dflt v = bits_df(row[k]);
-                sm[k] = (double)v.hi + (double)v.lo;
-            }
-        }
-        double c, sc;
-        bool ok;
-        if (ACC == LSEFIT_ACCUM_F64) {
-            ok = load_map_f64(p, s, c, sc);
-        } else {
-            float cf, sf;
-            ok = load_map_f32(p, s, cf, sf);
-            c = cf;
-            sc = sf;
-        }
-        const int nc = p.m_max + 1;
-        const int st = solve_hankel_rt<NMAX>(m, sm, sm + 2 * m + 1, c, sc, ok, p.eps,
-                                             p.Xt ? p.Xt + s * nc : nullptr, p.X + s * nc, nc);
-        p.status[s] = st;
-        if (p.sums) {
-            const double qnan = __longlong_as_double(0x7ff8000000000000ll);
-            const int stride = 3 * p.m_max + 2;
-            double* out = p.sums + s * stride;
-            for (int k = 0; k < stride; ++k) out[k] = k < ns ? (ok ? sm[k] : qnan) : 0.0;
-        }
-    }
+    unsigned char* base = reinterpret_cast<unsigned char*>(q.row);
+    // the queue of warp w of this block is at pend_block + w * kWarpBytes; solve
+    // entries relative to this warp's own queue
+    pend_solve_entry<NMAX, ACC>(p, base, 0, lane, lane < cnt);
     __syncwarp();
     if (lane == 0) *q.count = 0;
     __syncwarp();
@@ -234,15 +429,15 @@ __device__ void block_task(const BParams& p, int t, int4 task, dflt* red, double
         const bool ok = load_map_f64(p, s, c, sc);
         AccF64<M> A;
         A.init();
-        if (ok) accumulate_range_f64<M, DT, Unroll<M>::value, true>(A, p.x, p.y, b, e, tid, kBBlock, c, sc);
+        if (ok) accumulate_range_f64<M, DT, kBlockUnroll, true>(A, p.x, p.y, b, e, tid, kBBlock, c, sc);
         block_reduce_d<kBBlock, N>([&](int a) { return A.acc[a]; }, reinterpret_cast<double*>(red), blk);
         // blk[a] (doubles) == words[a]
     } else {
         float c, sc;
         const bool ok = load_map_f32(p, s, c, sc);
-        AccF32<M, ACC == LSEFIT_ACCUM_COMP> A;
+        AccF32<M, ACC == LSEFIT_ACCUM_COMP, true> A;
         A.init();
-        if (ok) accumulate_range<M, DT, ACC == LSEFIT_ACCUM_COMP, true, Unroll<M>::value>(
+        if (ok) accumulate_range<M, DT, ACC == LSEFIT_ACCUM_COMP, true, kBlockUnroll, true>(
             A, p.x, p.y, b, e, tid, kBBlock, c, sc);
         block_reduce_df2<kBBlock, N>([&](int a) { return A.result(a); }, red, reinterpret_cast<dflt*>(blk));
     }
@@ -306,34 +501,141 @@ __device__ void block_task(const BParams& p, int t, int4 task, dflt* red, double
 }
 
 // ---------------------------------------------------------------------------
-// One warp task: the whole of series s.
+// Accumulation of one stage from shared memory.  Buffer element j holds point
+// g0 + j (g0: r0 rounded down to a 16-byte vector); points outside
+// [r0, r0 + n) are masked out.
 // ---------------------------------------------------------------------------
+template <int M, int DT, bool COMP, bool SHL>
+__device__ __forceinline__ void stage_accumulate_f32(AccF32<M, COMP, SHL>& A, const unsigned char* xb,
+                                                     const unsigned char* yb, long long r0, int n, float cf,
+                                                     float sf) {
+    constexpr int PV = Elem<DT>::kPerVec, P = kStageBytes / Elem<DT>::kSize;
+    const int lane = threadIdx.x & 31;
+    const int lo = (int)(r0 & (PV - 1));
+    const int hi = lo + n;
+    const int nv = (hi + PV - 1) / PV;
+    const u64 c2 = pk2(cf, cf), s2 = pk2(sf, sf);
+    const bool full = (lo == 0 && n == P);
+#pragma unroll
+    for (int q = 0; q < kStageVecs / 32; ++q) {
+        const int v = lane + 32 * q;
+        if (v >= nv) continue;
+        const uint4 xv = *reinterpret_cast<const uint4*>(xb + 16 * v);
+        const uint4 yv = *reinterpret_cast<const uint4*>(yb + 16 * v);
+        if (full || (v * PV >= lo && (v + 1) * PV <= hi)) {
+            feed_vec<M, DT, COMP, true, false, SHL>(A, xv, yv, c2, s2);
+        } else {
+            float xs[PV], ys[PV];
+            if (DT == LSEFIT_F32) {
+                xs[0] = __uint_as_float(xv.x); xs[1] = __uint_as_float(xv.y);
+                xs[2 % PV] = __uint_as_float(xv.z); xs[3 % PV] = __uint_as_float(xv.w);
+                ys[0] = __uint_as_float(yv.x); ys[1] = __uint_as_float(yv.y);
+                ys[2 % PV] = __uint_as_float(yv.z); ys[3 % PV] = __uint_as_float(yv.w);
+            } else {
+                const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
+                const uint32_t yw[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+                for (int k = 0; k < PV / 2; ++k) {
+                    xs[2 * k] = bf16_lo(xw[k]); xs[2 * k + 1] = bf16_hi(xw[k]);
+                    ys[2 * k] = bf16_lo(yw[k]); ys[2 * k + 1] = bf16_hi(yw[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < PV; k += 2) {
+                const int e0 = v * PV + k, e1 = e0 + 1;
+                const bool ok0 = e0 >= lo && e0 < hi, ok1 = e1 >= lo && e1 < hi;
+                const float t0 = ok0 ? __fmul_rn(__fsub_rn(xs[k], cf), sf) : 0.0f;
+                const float t1 = ok1 ? __fmul_rn(__fsub_rn(xs[k + 1], cf), sf) : 0.0f;
+                A.template add_pair<false>(pk2(t0, t1), pk2(ok0 ? ys[k] : 0.0f, ok1 ? ys[k + 1] : 0.0f));
+            }
+        }
+    }
+}
+
+template <int M, int DT>
+__device__ __forceinline__ void stage_accumulate_f64(AccF64<M>& A, const unsigned char* xb,
+                                                     const unsigned char* yb, long long r0, int n, double c,
+                                                     double sc) {
+    constexpr int PV = Elem<DT>::kPerVec;
+    const int lane = threadIdx.x & 31;
+    const int lo = (int)(r0 & (PV - 1));
+    const int hi = lo + n;
+    const int nv = (hi + PV - 1) / PV;
+#pragma unroll
+    for (int q = 0; q < kStageVecs / 32; ++q) {
+        const int v = lane + 32 * q;
+        if (v >= nv) continue;
+        double xs[PV], ys[PV];
+        unpack_f64<DT, PV>(*reinterpret_cast<const uint4*>(xb + 16 * v), xs);
+        unpack_f64<DT, PV>(*reinterpret_cast<const uint4*>(yb + 16 * v), ys);
+#pragma unroll
+        for (int k = 0; k < PV; ++k) {
+            const int e = v * PV + k;
+            if (e >= lo && e < hi) A.add_point(sc * (xs[k] - c), ys[k]);
+        }
+    }
+}
+
+// One series streamed through the ring.  On entry the stage at `slot` is its
+// first stage and has landed; on return `slot` is the stage after its last.
 template <int NMAX, int DT, int ACC, int M>
-__device__ void warp_task(const BParams& p, int64_t s, Pend<NMAX>& q) {
+__device__ void ring_task(const BParams& p, Ring& R, int& slot, int& pending, Cursor& cu, Pend<NMAX>& q) {
     constexpr int N = 3 * M + 1;
     constexpr int NP = N <= 16 ? 16 : 32;
     const int lane = threadIdx.x & 31;
-    const int64_t b = p.offsets[s], e = p.offsets[s + 1];
-    const int slot = *q.count;
-    unsigned long long* row = q.row + slot * PendLayout<NMAX>::kStride;
+    const int s = R.rec[slot].s;
+    const double2 mraw = R.rec[slot].map;
+    long long count = 0;
     if constexpr (ACC == LSEFIT_ACCUM_F64) {
-        double c, sc;
-        const bool ok = load_map_f64(p, s, c, sc);
+        const bool ok = !isnan(mraw.x);
+        const double c = ok ? mraw.x : 0.0, sc = ok ? mraw.y : 1.0;
         AccF64<M> A;
         A.init();
-        if (ok) accumulate_range_f64<M, DT, Unroll<M>::value, true>(A, p.x, p.y, b, e, lane, 32, c, sc);
+        for (;;) {
+            const long long r0 = R.rec[slot].r0;
+            const int n = R.rec[slot].n, flags = R.rec[slot].flags;
+            if (ok) stage_accumulate_f64<M, DT>(A, R.x + slot * kStageBytes, R.y + slot * kStageBytes, r0, n, c, sc);
+            count += n;
+            __syncwarp();
+            --pending;
+            if (issue_stage<DT>(p, R, slot, cu)) ++pending;
+            slot = slot + 1 == kRing ? 0 : slot + 1;
+            if (flags & 2) break;
+            ring_wait(pending);
+        }
         double v[NP];
 #pragma unroll
         for (int a = 0; a < NP; ++a) v[a] = a < N ? A.acc[a] : 0.0;
         const double tot = warp_reduce_scatter_d<NP>(v);
+        const int qs = *q.count;
+        unsigned long long* row = q.row + qs * PendLayout<NMAX>::kStride;
         if (lane < N) row[lane + 1] = (unsigned long long)__double_as_longlong(tot);
     } else {
-        float c, sc;
-        const bool ok = load_map_f32(p, s, c, sc);
-        AccF32<M, ACC == LSEFIT_ACCUM_COMP> A;
+        const float2 mf = *reinterpret_cast<const float2*>(&mraw);
+        const bool ok = !isnan(mf.x);
+        const float c = ok ? mf.x : 0.0f, sc = ok ? mf.y : 1.0f;
+        AccF32<M, ACC == LSEFIT_ACCUM_COMP, true> A;
         A.init();
-        if (ok) accumulate_range<M, DT, ACC == LSEFIT_ACCUM_COMP, true, Unroll<M>::value>(
-            A, p.x, p.y, b, e, lane, 32, c, sc);
+        int since_fold = 0;
+        for (;;) {
+            const long long r0 = R.rec[slot].r0;
+            const int n = R.rec[slot].n, flags = R.rec[slot].flags;
+            if (ok)
+                stage_accumulate_f32<M, DT, ACC == LSEFIT_ACCUM_COMP, true>(A, R.x + slot * kStageBytes,
+                                                                            R.y + slot * kStageBytes, r0, n, c, sc);
+            if (++since_fold == kFoldStages) {
+                A.fold_reset();
+                since_fold = 0;
+            }
+            count += n;
+            __syncwarp();
+            --pending;
+            if (issue_stage<DT>(p, R, slot, cu)) ++pending;
+            slot = slot + 1 == kRing ? 0 : slot + 1;
+            if (flags & 2) break;
+            ring_wait(pending);
+        }
+        if (since_fold) A.fold_reset();
         dflt v[NP];
 #pragma unroll
         for (int a = 0; a < NP; ++a) {
@@ -345,16 +647,40 @@ __device__ void warp_task(const BParams& p, int64_t s, Pend<NMAX>& q) {
             }
         }
         const dflt tot = warp_reduce_scatter_df<NP>(v);
+        const int qs = *q.count;
+        unsigned long long* row = q.row + qs * PendLayout<NMAX>::kStride;
         if (lane < N) row[lane + 1] = df_bits(tot);
     }
     if (lane == 0) {
-        row[0] = (unsigned long long)(e - b);
-        q.sid[slot] = (int)s;
-        q.meta[slot] = M;
-        *q.count = slot + 1;
+        const int qs = *q.count;
+        q.row[qs * PendLayout<NMAX>::kStride] = (unsigned long long)count;
+        q.sid[qs] = s;
+        q.meta[qs] = M;
+        *q.count = qs + 1;
     }
     __syncwarp();
     if (*q.count == 32) pend_solve<NMAX, ACC>(p, q);
+}
+
+template <int NMAX, int DT, int ACC>
+__device__ __forceinline__ void dispatch_ring(const BParams& p, int m, Ring& R, int& slot, int& pending,
+                                              Cursor& cu, Pend<NMAX>& q) {
+    switch (m) {
+        case 1: ring_task<NMAX, DT, ACC, 1>(p, R, slot, pending, cu, q); break;
+        case 2: ring_task<NMAX, DT, ACC, 2>(p, R, slot, pending, cu, q); break;
+        case 3: ring_task<NMAX, DT, ACC, 3>(p, R, slot, pending, cu, q); break;
+        case 4: ring_task<NMAX, DT, ACC, 4>(p, R, slot, pending, cu, q); break;
+        case 5: ring_task<NMAX, DT, ACC, 5>(p, R, slot, pending, cu, q); break;
+        default:
+            if constexpr (NMAX > 5) {
+                switch (m) {
+                    case 6: ring_task<NMAX, DT, ACC, 6>(p, R, slot, pending, cu, q); break;
+                    case 7: ring_task<NMAX, DT, ACC, 7>(p, R, slot, pending, cu, q); break;
+                    default: ring_task<NMAX, DT, ACC, 8>(p, R, slot, pending, cu, q); break;
+                }
+            }
+            break;
+    }
 }
 
 template <int NMAX, int DT, int ACC>
@@ -379,39 +705,20 @@ __device__ __forceinline__ void dispatch_block(const BParams& p, int t, int4 tas
 }
 
 template <int NMAX, int DT, int ACC>
-__device__ __forceinline__ void dispatch_warp(const BParams& p, int64_t s, int m, Pend<NMAX>& q) {
-    switch (m) {
-        case 1: warp_task<NMAX, DT, ACC, 1>(p, s, q); break;
-        case 2: warp_task<NMAX, DT, ACC, 2>(p, s, q); break;
-        case 3: warp_task<NMAX, DT, ACC, 3>(p, s, q); break;
-        case 4: warp_task<NMAX, DT, ACC, 4>(p, s, q); break;
-        case 5: warp_task<NMAX, DT, ACC, 5>(p, s, q); break;
-        default:
-            if constexpr (NMAX > 5) {
-                switch (m) {
-                    case 6: warp_task<NMAX, DT, ACC, 6>(p, s, q); break;
-                    case 7: warp_task<NMAX, DT, ACC, 7>(p, s, q); break;
-                    default: warp_task<NMAX, DT, ACC, 8>(p, s, q); break;
-                }
-            }
-            break;
-    }
-}
-
-template <int NMAX, int DT, int ACC>
-__global__ void __launch_bounds__(kBBlock, NMAX <= 5 ? 2 : 1) batched_kernel(BParams p) {
+__global__ void __launch_bounds__(kBBlock, 1) batched_kernel(BParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_task;
     __shared__ int s_last;
     dflt* red = reinterpret_cast<dflt*>(smem);
-    double* blk = reinterpret_cast<double*>(smem + kRedBytes);
+    double* blk = reinterpret_cast<double*>(smem + kScratchBytes);
     double* comb = blk + 32;
-    unsigned char* pend_base = reinterpret_cast<unsigned char*>(comb + 32);
+    int* counts = reinterpret_cast<int*>(comb + 32);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* pend_block = p.pend + (size_t)blockIdx.x * kBWarps * PendLayout<NMAX>::kWarpBytes;
     Pend<NMAX> q;
-    q.bind(pend_base + warp * PendLayout<NMAX>::kBytes);
+    q.bind(pend_block + warp * PendLayout<NMAX>::kWarpBytes, counts + warp);
     Pend<NMAX> q0;
-    q0.bind(pend_base);
+    q0.bind(pend_block, counts);
     if (lane == 0) *q.count = 0;
     __syncthreads();
 
@@ -430,22 +737,44 @@ __global__ void __launch_bounds__(kBBlock, NMAX <= 5 ? 2 : 1) batched_kernel(BPa
         }
         dispatch_block<NMAX, DT, ACC>(p, t, task, m, red, blk, comb, q0, &s_last);
     }
-    // phase 2: warp tasks
-    for (;;) {
-        int t = 0;
-        if (lane == 0) t = (int)atomicAdd(&p.counters[1], 1u);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= p.n_warp_tasks) break;
-        const int64_t s = p.warp_tasks[t];
-        const int m = p.degree[s];
-        if (m < 1 || m > p.m_max || m > NMAX) {
-            if (lane == 0) mark_invalid(p, s);
-            continue;
+    // phase 2: warp tasks through the warp's stage ring
+    {
+        Ring R;
+        R.bind(smem + warp * kRingWarpBytes);
+        Cursor cu;
+        cu.wid = blockIdx.x * kBWarps + warp;
+        cu.nw = gridDim.x * kBWarps;
+        cu.round = 0;
+        cu.have = false;
+        cu.bv = false;
+        cursor_fetch_record(cu, p);
+        cursor_advance(cu, p);  // a -> b
+        cursor_advance(cu, p);  // b -> current
+        int pending = 0;
+#pragma unroll
+        for (int k = 0; k < kRing; ++k)
+            if (issue_stage<DT>(p, R, k, cu)) ++pending;
+        int slot = 0;
+        while (pending > 0) {
+            ring_wait(pending);
+            dispatch_ring<NMAX, DT, ACC>(p, R.rec[slot].deg, R, slot, pending, cu, q);
         }
-        dispatch_warp<NMAX, DT, ACC>(p, s, m, q);
     }
-    __syncwarp();
-    if (*q.count > 0) pend_solve<NMAX, ACC>(p, q);
+    // leftover queued series of all warps, solved 32 per warp across the block
+    __syncthreads();
+    {
+        int total = 0;
+        for (int w = 0; w < kBWarps; ++w) total += counts[w];
+        for (int base = warp * 32; base < total; base += kBWarps * 32) {
+            const int g = base + lane;
+            int ws = 0, idx = g;
+            while (ws < kBWarps && idx >= counts[ws]) {
+                idx -= counts[ws];
+                ++ws;
+            }
+            pend_solve_entry<NMAX, ACC>(p, pend_block, ws, idx, g < total);
+        }
+    }
     __syncthreads();
     if (tid == 0) {
         __threadfence();

@@ -87,14 +87,28 @@ __device__ __forceinline__ dflt df_shfl_xor(dflt v, int mask) {
 
 __device__ __forceinline__ double df_to_double(dflt v) { return (double)v.hi + (double)v.lo; }
 
-// TwoSum on both lanes of a pair: (hi, lo) += b with the rounding error of
-// the high sum carried into lo.
-__device__ __forceinline__ void fold2(u64& hi, u64& lo, u64 b) {
-    u64 s = add2(hi, b);
-    u64 bb = sub2(s, hi);
-    u64 e = add2(sub2(hi, sub2(s, bb)), sub2(b, bb));
-    lo = add2(lo, e);
-    hi = s;
+// Exact FP32 -> FP64 conversion with integer operations (no FP64 pipe):
+// rebias the exponent and widen the significand; zero, subnormal, Inf and
+// NaN are handled by their encodings.
+__device__ __forceinline__ double f32_to_f64_int(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    const unsigned ex = (u >> 23) & 0xffu;
+    unsigned long long man = u & 0x7fffffu;
+    unsigned long long bits;
+    if (ex == 0xffu) {
+        bits = sign | (0x7ffull << 52) | (man << 29);  // Inf / NaN
+    } else if (ex != 0u) {
+        bits = sign | ((unsigned long long)(ex + 896u) << 52) | (man << 29);  // 896 = 1023 - 127
+    } else if (man == 0ull) {
+        bits = sign;  // signed zero
+    } else {
+        // subnormal FP32: normalise the significand (FP64 has the range)
+        const int lz = __clzll(man) - 40;  // leading zeros within the 23-bit field
+        man = (man << (lz + 1)) & 0x7fffffull;
+        bits = sign | ((unsigned long long)(896u - lz) << 52) | (man << 29);
+    }
+    return __longlong_as_double((long long)bits);
 }
 
 // ---------------------------------------------------------------------------
@@ -146,6 +160,20 @@ __device__ __forceinline__ uint4 ld_stream16(const void* p) {
 }
 
 // ---------------------------------------------------------------------------
+// Asynchronous global->shared copies (cp.async): in flight without holding
+// registers; cp.async.wait_group is a hardware wait on this thread's groups.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Map constants.  c = (lo + hi) / 2, s = 2 / (hi - lo) in FP64, rounded once
 // to FP32 when the points are mapped in FP32.  Identity without an interval.
 // Returns false for an interval that is not finite or has hi <= lo.
@@ -188,22 +216,34 @@ struct Nacc {
 };
 
 // FP32 pair accumulator: each u64 carries two independent lane sums.
-// COMP adds a (hi, lo) TwoSum pair per accumulator, fed once per batch.
-template <int M, bool COMP>
+// COMP adds a TwoSum pair (hi, lo) per accumulator, fed once per batch:
+//  * SHL = false: (hi, lo) are packed pairs too, one per lane (6 registers per
+//    accumulator; the fold is 7 packed instructions);
+//  * SHL = true: (hi, lo) are scalars; the two lanes of the batch sum are
+//    added first (one rounding of the batch's own size), then added to hi
+//    exactly (4 registers per accumulator; 8 scalar instructions).
+template <int M, bool COMP, bool SHL = false>
 struct AccF32 {
     static constexpr int N = 3 * M + 1;
     u64 acc[N];
-    u64 hi[COMP ? N : 1];
-    u64 lo[COMP ? N : 1];
+    u64 phi[(COMP && !SHL) ? N : 1], plo[(COMP && !SHL) ? N : 1];
+    float shi[(COMP && SHL) ? N : 1], slo[(COMP && SHL) ? N : 1];
 
     __device__ __forceinline__ void init() {
 #pragma unroll
         for (int a = 0; a < N; ++a) acc[a] = 0ull;
-        if (COMP) {
+        if (COMP && !SHL) {
 #pragma unroll
             for (int a = 0; a < N; ++a) {
-                hi[a] = 0ull;
-                lo[a] = 0ull;
+                phi[a] = 0ull;
+                plo[a] = 0ull;
+            }
+        }
+        if (COMP && SHL) {
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                shi[a] = 0.0f;
+                slo[a] = 0.0f;
             }
         }
     }
@@ -237,23 +277,51 @@ struct AccF32 {
 
     // Compensated mode: move the batch sums into the (hi, lo) pairs.
     __device__ __forceinline__ void fold() {
-        if (COMP) {
+        if (COMP && !SHL) {
 #pragma unroll
-            for (int a = 0; a < N; ++a) fold2(hi[a], lo[a], acc[a]);
+            for (int a = 0; a < N; ++a) {
+                const u64 b = acc[a];
+                const u64 s = add2(phi[a], b);
+                const u64 bb = sub2(s, phi[a]);
+                const u64 e = add2(sub2(phi[a], sub2(s, bb)), sub2(b, bb));
+                plo[a] = add2(plo[a], e);
+                phi[a] = s;
+            }
+        }
+        if (COMP && SHL) {
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                float x0, x1, sh, e;
+                up2(acc[a], x0, x1);
+                two_sum(shi[a], __fadd_rn(x0, x1), sh, e);
+                shi[a] = sh;
+                slo[a] = __fadd_rn(slo[a], e);
+            }
+        }
+    }
+    // As fold(), and restart the batch at zero (batches fed with add_pair<false>).
+    __device__ __forceinline__ void fold_reset() {
+        if (COMP) {
+            fold();
+#pragma unroll
+            for (int a = 0; a < N; ++a) acc[a] = 0ull;
         }
     }
 
-    // Final per-thread value of accumulator a as double-float (both lanes).
+    // Final per-thread value of accumulator a as double-float.
     __device__ __forceinline__ dflt result(int a) const {
-        float x0, x1;
         dflt r;
-        if (COMP) {
-            float l0, l1;
-            up2(hi[a], x0, x1);
-            up2(lo[a], l0, l1);
-            dflt u = {x0, l0}, v = {x1, l1};
+        if (COMP && !SHL) {
+            float x0, x1, l0, l1;
+            up2(phi[a], x0, x1);
+            up2(plo[a], l0, l1);
+            const dflt u = {x0, l0}, v = {x1, l1};
             r = df_add(u, v);
+        } else if (COMP) {
+            r.hi = shi[a];
+            r.lo = slo[a];
         } else {
+            float x0, x1;
             up2(acc[a], x0, x1);
             two_sum(x0, x1, r.hi, r.lo);
         }
@@ -441,18 +509,15 @@ __device__ __forceinline__ int hankel_ge(int m, const double* S, const double* r
     constexpr int N = NMAX + 1;
     int st = LSEFIT_OK;
     double A[N][N + 1];
+    // max|A| over the 2m+1 distinct entries S_0..S_2m of the Hankel matrix
     double amax = 0.0;
+#pragma unroll
+    for (int k = 0; k <= 2 * NMAX; ++k)
+        if (k <= 2 * m) amax = fmax(amax, fabs(S[k]));
 #pragma unroll
     for (int j = 0; j < N; ++j) {
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
-            double v = (j == k) ? 1.0 : 0.0;
-            if (j <= m && k <= m) {
-                v = S[j + k];
-                amax = fmax(amax, fabs(v));
-            }
-            A[j][k] = v;
-        }
+        for (int k = 0; k < N; ++k) A[j][k] = (j <= m && k <= m) ? S[j + k] : ((j == k) ? 1.0 : 0.0);
         A[j][N] = (j <= m) ? rhs[j] : 0.0;
     }
     const double tol = (double)(m + 1) * eps * amax;
@@ -598,8 +663,8 @@ __device__ __forceinline__ void split_range(const void* x, const void* y, int64_
 }
 
 // Unpack one 16-byte vector of x and of y into packed pairs and feed them.
-template <int M, int DT, bool COMP, bool MAP, bool FIRST>
-__device__ __forceinline__ void feed_vec(AccF32<M, COMP>& A, uint4 xv, uint4 yv, u64 c2, u64 s2) {
+template <int M, int DT, bool COMP, bool MAP, bool FIRST, bool SHL = false>
+__device__ __forceinline__ void feed_vec(AccF32<M, COMP, SHL>& A, uint4 xv, uint4 yv, u64 c2, u64 s2) {
     if (DT == LSEFIT_F32) {
         u64 xa = pk2(__uint_as_float(xv.x), __uint_as_float(xv.y));
         u64 xb = pk2(__uint_as_float(xv.z), __uint_as_float(xv.w));
@@ -627,8 +692,8 @@ __device__ __forceinline__ void feed_vec(AccF32<M, COMP>& A, uint4 xv, uint4 yv,
 
 // FP32/BF16 storage, FP32 arithmetic.  In compensated mode each thread's
 // batch (UNROLL vectors, or one scalar point) is folded into its TwoSum pairs.
-template <int M, int DT, bool COMP, bool MAP, int UNROLL>
-__device__ __forceinline__ void accumulate_range(AccF32<M, COMP>& A, const void* x, const void* y,
+template <int M, int DT, bool COMP, bool MAP, int UNROLL, bool SHL = false>
+__device__ __forceinline__ void accumulate_range(AccF32<M, COMP, SHL>& A, const void* x, const void* y,
                                                  int64_t b, int64_t e, int64_t rank, int64_t nthreads,
                                                  float cf, float sf) {
     constexpr int ES = Elem<DT>::kSize, PV = Elem<DT>::kPerVec;
@@ -647,13 +712,13 @@ __device__ __forceinline__ void accumulate_range(AccF32<M, COMP>& A, const void*
         }
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {
-            if (u == 0) feed_vec<M, DT, COMP, MAP, COMP>(A, xr[u], yr[u], c2, s2);
-            else feed_vec<M, DT, COMP, MAP, false>(A, xr[u], yr[u], c2, s2);
+            if (u == 0) feed_vec<M, DT, COMP, MAP, COMP, SHL>(A, xr[u], yr[u], c2, s2);
+            else feed_vec<M, DT, COMP, MAP, false, SHL>(A, xr[u], yr[u], c2, s2);
         }
         A.fold();
     }
     for (; v < nvec; v += nthreads) {
-        feed_vec<M, DT, COMP, MAP, COMP>(A, ld_stream16(xv + v), ld_stream16(yv + v), c2, s2);
+        feed_vec<M, DT, COMP, MAP, COMP, SHL>(A, ld_stream16(xv + v), ld_stream16(yv + v), c2, s2);
         A.fold();
     }
     // scalar points: [b, b + head) and [b + head + nvec * PV, e)

@@ -1,0 +1,352 @@
+// lsefit_residuals.cu -- fitted values and residual errors of a batched fit.
+//
+// Section III judges a fit by its residuals e_i = y_i - f(x_i) and their sum
+// of squares (Table V, the figures printed under it).  One more pass over the
+// points gives, per series, SSE = sum_i r_i^2 and the orthogonality
+// diagnostics (V^T r)_k = sum_i t_i^k r_i (k = 0..m), which vanish at the
+// least-squares solution (the normal equations of Section II), and
+// optionally the residuals themselves.  f is evaluated in the mapped basis:
+// f(x_i) = sum_k Xt_k t_i^k, t_i = s (x_i - c), by Horner's rule.
+//
+// Accumulation: FP32 per point, compensated double-float per thread
+// (TwoSum per small batch), double-float warp/block reductions, FP64 chunk
+// partials combined in chunk order by the block that completes a split
+// series (ticket, no waiting).  FP64 data use FP64 throughout.
+#include "lsefit_device.cuh"
+#include "lsefit_host.h"
+
+namespace lsefit {
+
+constexpr int kRsBlock = 256;
+
+struct RsParams {
+    const void* x;
+    const void* y;
+    const int64_t* offsets;
+    const int32_t* degree;
+    int64_t num_series;
+    int m_max;
+    const double* Xt;    // [S][m_max+1]
+    const double* map;   // [S][2] or null (identity)
+    const int4* block_tasks;
+    int n_block_tasks;
+    const int4* warp_tasks;
+    int n_warp_tasks;
+    void* r;             // per-point residuals (FP32, or FP64 for FP64 data) or null
+    double* sse;         // [S]
+    double* vtr;         // [S][m_max+1] or null
+    double* partials;    // [n_block_tasks][m_max+2]
+    unsigned* tickets;   // [n_block_tasks]
+    unsigned* counters;  // [0] block queue, [1] warp queue, [2] exited blocks
+};
+
+// Per-thread sums: a = 0 -> r^2, a = 1 + k -> t^k r.
+template <int M>
+struct RsAcc {
+    static constexpr int N = M + 2;
+    float bh[N];  // batch sums
+    float hi[N], lo[N];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            bh[a] = 0.0f;
+            hi[a] = 0.0f;
+            lo[a] = 0.0f;
+        }
+    }
+    __device__ __forceinline__ void add(float t, float r) {
+        bh[0] = fmaf(r, r, bh[0]);
+        float p = r;
+#pragma unroll
+        for (int k = 0; k <= M; ++k) {
+            bh[1 + k] += p;
+            p *= t;
+        }
+    }
+    __device__ __forceinline__ void fold() {
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            float s, e;
+            two_sum(hi[a], bh[a], s, e);
+            hi[a] = s;
+            lo[a] = __fadd_rn(lo[a], e);
+            bh[a] = 0.0f;
+        }
+    }
+};
+
+template <int M>
+__device__ __forceinline__ float horner(const float* a, float t) {
+    float v = a[M];
+#pragma unroll
+    for (int j = M - 1; j >= 0; --j) v = fmaf(v, t, a[j]);
+    return v;
+}
+
+template <int DT, int M>
+__device__ __forceinline__ void rs_range_f32(const RsParams& p, int64_t s, int64_t b, int64_t e, int64_t rank,
+                                             int64_t nthreads, RsAcc<M>& A) {
+    const int nc = p.m_max + 1;
+    float coef[M + 1];
+#pragma unroll
+    for (int j = 0; j <= M; ++j) coef[j] = (float)p.Xt[s * nc + j];
+    const float c = p.map ? (float)p.map[2 * s] : 0.0f;
+    const float sc = p.map ? (float)p.map[2 * s + 1] : 1.0f;
+    float* rout = static_cast<float*>(p.r);
+    int batch = 0;
+    for (int64_t i = b + rank; i < e; i += nthreads) {
+        const float t = __fmul_rn(__fsub_rn(Elem<DT>::ld(p.x, i), c), sc);
+        const float r = __fsub_rn(Elem<DT>::ld(p.y, i), horner<M>(coef, t));
+        if (rout) rout[i] = r;
+        A.add(t, r);
+        if (++batch == 8) {
+            A.fold();
+            batch = 0;
+        }
+    }
+    A.fold();
+}
+
+template <int M>
+__device__ __forceinline__ void rs_range_f64(const RsParams& p, int64_t s, int64_t b, int64_t e, int64_t rank,
+                                             int64_t nthreads, double* acc) {
+    const int nc = p.m_max + 1;
+    double coef[M + 1];
+#pragma unroll
+    for (int j = 0; j <= M; ++j) coef[j] = p.Xt[s * nc + j];
+    const double c = p.map ? p.map[2 * s] : 0.0;
+    const double sc = p.map ? p.map[2 * s + 1] : 1.0;
+    double* rout = static_cast<double*>(p.r);
+    for (int64_t i = b + rank; i < e; i += nthreads) {
+        const double t = sc * (Elem<LSEFIT_F64>::ld64(p.x, i) - c);
+        double f = coef[M];
+#pragma unroll
+        for (int j = M - 1; j >= 0; --j) f = fma(f, t, coef[j]);
+        const double r = Elem<LSEFIT_F64>::ld64(p.y, i) - f;
+        if (rout) rout[i] = r;
+        acc[0] = fma(r, r, acc[0]);
+        double q = r;
+#pragma unroll
+        for (int k = 0; k <= M; ++k) {
+            acc[1 + k] += q;
+            q *= t;
+        }
+    }
+}
+
+// Write the totals of series s (FP64), padding vtr with zeros.
+__device__ __forceinline__ void rs_store(const RsParams& p, int64_t s, int M, const double* tot, bool ok) {
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    p.sse[s] = ok ? tot[0] : qnan;
+    if (p.vtr) {
+        const int nc = p.m_max + 1;
+        for (int k = 0; k < nc; ++k) p.vtr[s * nc + k] = (ok && k <= M) ? tot[1 + k] : (k <= M ? qnan : 0.0);
+    }
+}
+
+template <int DT, int M>
+__device__ void rs_block_task(const RsParams& p, int t, int4 task, dflt* red, double* red64, double* tot,
+                              int* s_last) {
+    constexpr int N = M + 2;
+    const int tid = threadIdx.x;
+    const int64_t s = task.x;
+    const int chunk = task.y, nch = task.z, first = task.w;
+    const int64_t b0 = p.offsets[s], e0 = p.offsets[s + 1];
+    const int64_t per = ((e0 - b0 + nch - 1) / nch + 7) / 8 * 8;
+    const int64_t b = min(b0 + (int64_t)chunk * per, e0), e = min(b + per, e0);
+    if constexpr (DT == LSEFIT_F64) {
+        double acc[N];
+#pragma unroll
+        for (int a = 0; a < N; ++a) acc[a] = 0.0;
+        rs_range_f64<M>(p, s, b, e, tid, kRsBlock, acc);
+        block_reduce_d<kRsBlock, N>([&](int a) { return acc[a]; }, red64, tot);
+    } else {
+        RsAcc<M> A;
+        A.init();
+        rs_range_f32<DT, M>(p, s, b, e, tid, kRsBlock, A);
+        block_reduce_df<kRsBlock, N>([&](int a) { dflt v = {A.hi[a], A.lo[a]}; return v; }, red, tot);
+    }
+    const bool ok = isfinite(p.Xt[s * (p.m_max + 1)]);
+    if (nch == 1) {
+        if (tid == 0) rs_store(p, s, M, tot, ok);
+        return;
+    }
+    const int stride = p.m_max + 2;
+    if (tid < N) {
+        p.partials[(size_t)t * stride + tid] = tot[tid];
+        __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) *s_last = (atomicAdd(&p.tickets[first], 1u) == (unsigned)(nch - 1));
+    __syncthreads();
+    if (*s_last) {
+        __threadfence();
+        if (tid < N) {
+            double v = 0.0;
+            for (int k = 0; k < nch; ++k) v += __ldcg(p.partials + (size_t)(first + k) * stride + tid);
+            tot[tid] = v;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            rs_store(p, s, M, tot, ok);
+            p.tickets[first] = 0u;
+        }
+    }
+}
+
+template <int DT, int M>
+__device__ void rs_warp_task(const RsParams& p, int64_t s) {
+    constexpr int N = M + 2;
+    const int lane = threadIdx.x & 31;
+    const int64_t b = p.offsets[s], e = p.offsets[s + 1];
+    double tot[N];
+    if constexpr (DT == LSEFIT_F64) {
+        double acc[N];
+#pragma unroll
+        for (int a = 0; a < N; ++a) acc[a] = 0.0;
+        rs_range_f64<M>(p, s, b, e, lane, 32, acc);
+#pragma unroll
+        for (int a = 0; a < N; ++a) tot[a] = warp_reduce_d(acc[a]);
+    } else {
+        RsAcc<M> A;
+        A.init();
+        rs_range_f32<DT, M>(p, s, b, e, lane, 32, A);
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            const dflt v = {A.hi[a], A.lo[a]};
+            tot[a] = df_to_double(warp_reduce_df(v));
+        }
+    }
+    if (lane == 0) rs_store(p, s, M, tot, isfinite(p.Xt[s * (p.m_max + 1)]));
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kRsBlock) residuals_kernel(RsParams p) {
+    __shared__ int s_task;
+    __shared__ int s_last;
+    __shared__ dflt red[(kRsBlock / 32) * kRsBlock];
+    __shared__ double tot[16];
+    const int tid = threadIdx.x, lane = tid & 31;
+    double* red64 = reinterpret_cast<double*>(red);
+    for (;;) {
+        if (tid == 0) s_task = (int)atomicAdd(&p.counters[0], 1u);
+        __syncthreads();
+        const int t = s_task;
+        __syncthreads();
+        if (t >= p.n_block_tasks) break;
+        const int4 task = p.block_tasks[t];
+        const int m = p.degree[task.x];
+        switch (m) {
+            case 1: rs_block_task<DT, 1>(p, t, task, red, red64, tot, &s_last); break;
+            case 2: rs_block_task<DT, 2>(p, t, task, red, red64, tot, &s_last); break;
+            case 3: rs_block_task<DT, 3>(p, t, task, red, red64, tot, &s_last); break;
+            case 4: rs_block_task<DT, 4>(p, t, task, red, red64, tot, &s_last); break;
+            case 5: rs_block_task<DT, 5>(p, t, task, red, red64, tot, &s_last); break;
+            case 6: rs_block_task<DT, 6>(p, t, task, red, red64, tot, &s_last); break;
+            case 7: rs_block_task<DT, 7>(p, t, task, red, red64, tot, &s_last); break;
+            case 8: rs_block_task<DT, 8>(p, t, task, red, red64, tot, &s_last); break;
+            default:
+                if (tid == 0 && task.y == 0) p.sse[task.x] = __longlong_as_double(0x7ff8000000000000ll);
+                break;
+        }
+        __syncthreads();
+    }
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = (int)atomicAdd(&p.counters[1], 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= p.n_warp_tasks) break;
+        const int64_t s = p.warp_tasks[t].x;
+        switch (p.degree[s]) {
+            case 1: rs_warp_task<DT, 1>(p, s); break;
+            case 2: rs_warp_task<DT, 2>(p, s); break;
+            case 3: rs_warp_task<DT, 3>(p, s); break;
+            case 4: rs_warp_task<DT, 4>(p, s); break;
+            case 5: rs_warp_task<DT, 5>(p, s); break;
+            case 6: rs_warp_task<DT, 6>(p, s); break;
+            case 7: rs_warp_task<DT, 7>(p, s); break;
+            case 8: rs_warp_task<DT, 8>(p, s); break;
+            default:
+                if (lane == 0) p.sse[s] = __longlong_as_double(0x7ff8000000000000ll);
+                break;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&p.counters[2], 1u) == gridDim.x - 1) {
+            p.counters[0] = 0u;
+            p.counters[1] = 0u;
+            p.counters[2] = 0u;
+        }
+    }
+}
+
+__global__ void residuals_prep_kernel(unsigned* counters, unsigned* tickets, int n_block_tasks) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 3) counters[i] = 0u;
+    if (i < n_block_tasks) tickets[i] = 0u;
+}
+
+}  // namespace lsefit
+
+using namespace lsefit;
+
+// Workspace: counters | tickets [nbt] | FP64 partials [nbt][m_max+2].
+extern "C" size_t lsefit_residuals_workspace_size(const lsefit_plan* plan) {
+    if (plan == nullptr || plan->n_block_tasks < 0 || plan->m_max < 1) return 0;
+    const size_t nbt = (size_t)plan->n_block_tasks;
+    return kAlign + align_up(nbt * sizeof(unsigned), kAlign) + align_up(nbt * (plan->m_max + 2) * sizeof(double), kAlign);
+}
+
+extern "C" int lsefit_residuals(const lsefit_batch* batch, const lsefit_plan* plan, const double* Xt,
+                                const double* map, void* r, double* sse, double* vtr, void* workspace,
+                                size_t workspace_bytes, lsefit_stream_t stream) {
+    if (batch == nullptr || plan == nullptr || Xt == nullptr || sse == nullptr) return LSEFIT_ERR_INVALID_ARG;
+    const lsefit_batch& b = *batch;
+    if (b.num_series != plan->num_series || b.m_max != plan->m_max || b.m_max < 1 || b.m_max > LSEFIT_MAX_DEGREE)
+        return LSEFIT_ERR_INVALID_ARG;
+    if (b.dtype < LSEFIT_F64 || b.dtype > LSEFIT_BF16) return LSEFIT_ERR_INVALID_ARG;
+    if (b.num_series == 0) return LSEFIT_OK;
+    if (b.offsets == nullptr || b.degree == nullptr) return LSEFIT_ERR_INVALID_ARG;
+    if (plan->total_points > 0 && (b.x == nullptr || b.y == nullptr)) return LSEFIT_ERR_INVALID_ARG;
+    if (workspace == nullptr || !aligned(workspace, kAlign) ||
+        workspace_bytes < lsefit_residuals_workspace_size(plan))
+        return LSEFIT_ERR_WORKSPACE;
+    RsParams p;
+    p.x = b.x;
+    p.y = b.y;
+    p.offsets = b.offsets;
+    p.degree = b.degree;
+    p.num_series = b.num_series;
+    p.m_max = b.m_max;
+    p.Xt = Xt;
+    p.map = map;
+    p.block_tasks = reinterpret_cast<const int4*>(plan->block_tasks);
+    p.n_block_tasks = plan->n_block_tasks;
+    p.warp_tasks = reinterpret_cast<const int4*>(plan->warp_tasks);
+    p.n_warp_tasks = plan->n_warp_tasks;
+    p.r = r;
+    p.sse = sse;
+    p.vtr = vtr;
+    char* ws = static_cast<char*>(workspace);
+    p.counters = reinterpret_cast<unsigned*>(ws);
+    p.tickets = reinterpret_cast<unsigned*>(ws + kAlign);
+    p.partials = reinterpret_cast<double*>(ws + kAlign + align_up((size_t)plan->n_block_tasks * sizeof(unsigned), kAlign));
+    const int items = plan->n_block_tasks > 3 ? plan->n_block_tasks : 3;
+    residuals_prep_kernel<<<(items + 255) / 256, 256, 0, (cudaStream_t)stream>>>(p.counters, p.tickets,
+                                                                               plan->n_block_tasks);
+    if (cudaGetLastError() != cudaSuccess) return LSEFIT_ERR_CUDA;
+    auto k = b.dtype == LSEFIT_F64 ? residuals_kernel<LSEFIT_F64>
+             : b.dtype == LSEFIT_F32 ? residuals_kernel<LSEFIT_F32> : residuals_kernel<LSEFIT_BF16>;
+    int dev = 0;
+    const int sms = current_sm_count(&dev);
+    if (sms <= 0) return LSEFIT_ERR_CUDA;
+    const int occ = occupancy_blocks(reinterpret_cast<const void*>(k), kRsBlock, 0);
+    int64_t grid = (int64_t)sms * occ;
+    const int64_t useful = (int64_t)plan->n_block_tasks + (plan->n_warp_tasks + 7) / 8;
+    if (useful < grid) grid = useful;
+    if (grid < 1) grid = 1;
+    k<<<(unsigned)grid, kRsBlock, 0, (cudaStream_t)stream>>>(p);
+    return cudaGetLastError() == cudaSuccess ? LSEFIT_OK : LSEFIT_ERR_CUDA;
+}

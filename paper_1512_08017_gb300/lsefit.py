@@ -87,9 +87,13 @@ SIGNATURES = {
     "lsefit_fit": (_INT, [_VP, _VP, _I64, _INT, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "lsefit_fit_noalloc_scratch_bytes": (_SZ, []),
     "lsefit_fit_noalloc": (_INT, [_VP, _VP, _I64, _INT, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
-    "lsefit_plan_build": (_INT, [_VP, _I64, _INT, _VP, _INT, _VP, _VP, _I64, _VP, _I64]),
+    "lsefit_plan_build": (_INT, [_VP, _VP, _I64, _INT, _VP, _INT, _VP, _VP, _I64, _VP, _I64]),
     "lsefit_batched_workspace_size": (_SZ, [_VP]),
     "lsefit_fit_batched": (_INT, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "lsefit_residuals_workspace_size": (_SZ, [_VP]),
+    "lsefit_residuals": (_INT, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "lsefit_range_workspace_size": (_SZ, [_VP]),
+    "lsefit_range": (_INT, [_VP, _VP, _VP, _VP, _SZ, _VP]),
     "lsefit_backward_workspace_size": (_SZ, [_VP]),
     "lsefit_backward": (_INT, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
 }
@@ -304,9 +308,14 @@ class BatchPlan:
     Built once per layout (offsets) and reused by every fit of that layout,
     including CUDA graph replays."""
 
-    def __init__(self, offsets, m_max: int, tuning: dict | None = None, device=None):
+    def __init__(self, offsets, m_max: int, tuning: dict | None = None, device=None, degree=None):
         import numpy as np
         off = _as_host_int64(offsets)
+        deg = None
+        if degree is not None:
+            deg = np.ascontiguousarray(
+                degree.detach().cpu().numpy() if isinstance(degree, torch.Tensor) else degree, dtype=np.int32)
+        degp = deg.ctypes.data_as(ctypes.c_void_p) if deg is not None else None
         S = off.size - 1
         device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         sms = torch.cuda.get_device_properties(device).multi_processor_count
@@ -315,19 +324,19 @@ class BatchPlan:
             setattr(tun, k, int(v))
         plan = Plan()
         offp = off.ctypes.data_as(ctypes.c_void_p)
-        rc = lib.lsefit_plan_build(offp, S, int(m_max), ctypes.byref(tun), sms, ctypes.byref(plan),
+        rc = lib.lsefit_plan_build(offp, degp, S, int(m_max), ctypes.byref(tun), sms, ctypes.byref(plan),
                                    None, 0, None, 0)
         if rc not in (OK, ERR_WORKSPACE):
             _check(rc, "lsefit_plan_build")
         nb, nw = plan.n_block_tasks, plan.n_warp_tasks
         bt = np.zeros(max(4 * nb, 4), dtype=np.int32)
-        wt = np.zeros(max(nw, 1), dtype=np.int32)
-        rc = lib.lsefit_plan_build(offp, S, int(m_max), ctypes.byref(tun), sms, ctypes.byref(plan),
+        wt = np.zeros(max(4 * nw, 4), dtype=np.int32)
+        rc = lib.lsefit_plan_build(offp, degp, S, int(m_max), ctypes.byref(tun), sms, ctypes.byref(plan),
                                    bt.ctypes.data_as(ctypes.c_void_p), nb,
                                    wt.ctypes.data_as(ctypes.c_void_p), nw)
         _check(rc, "lsefit_plan_build")
         self.block_tasks_host = bt[: 4 * nb].reshape(-1, 4)
-        self.warp_tasks_host = wt[:nw]
+        self.warp_tasks_host = wt[: 4 * nw].reshape(-1, 4)
         self.block_tasks = torch.from_numpy(bt).to(device)
         self.warp_tasks = torch.from_numpy(wt).to(device)
         plan.block_tasks = self.block_tasks.data_ptr()
@@ -372,7 +381,8 @@ def fit_batched(x, y, offsets, degree, interval=None, m_max: int | None = None, 
     if m_max is None:
         m_max = int(deg_d.max().item()) if S > 0 else 1
     if plan is None:
-        plan = BatchPlan(offsets if not isinstance(offsets, torch.Tensor) else off_d, m_max, device=dev)
+        plan = BatchPlan(offsets if not isinstance(offsets, torch.Tensor) else off_d, m_max, device=dev,
+                         degree=degree)
     if plan.num_series != S or plan.m_max != m_max:
         raise ValueError("plan does not match the batch")
     iv = None
@@ -398,6 +408,52 @@ def fit_batched(x, y, offsets, degree, interval=None, m_max: int | None = None, 
     out["plan"] = plan
     # keep the device copies alive for asynchronous use
     out["_inputs"] = (off_d, deg_d, iv)
+    return out
+
+
+def residuals_batched(x, y, offsets, degree, fwd: dict, want_r: bool = False, want_vtr: bool = True,
+                      interval_given: bool = True, stream=None) -> dict:
+    """SSE, V^T r and optionally the residuals of a batched fit (lsefit_residuals).
+
+    fwd is the dict returned by fit_batched (its plan, Xt and map are used)."""
+    plan: BatchPlan = fwd["plan"]
+    dev = x.device
+    off_d = _to_device(offsets, torch.int64, dev)
+    deg_d = _to_device(degree, torch.int32, dev)
+    S = off_d.numel() - 1
+    out = {"sse": torch.empty(S, dtype=torch.float64, device=dev)}
+    if want_vtr:
+        out["vtr"] = torch.empty(S, plan.m_max + 1, dtype=torch.float64, device=dev)
+    if want_r:
+        out["r"] = torch.empty(x.shape, dtype=torch.float64 if x.dtype == torch.float64 else torch.float32,
+                               device=dev)
+    b = Batch(x.data_ptr(), y.data_ptr(), off_d.data_ptr(), deg_d.data_ptr(), None, S, plan.m_max,
+              _dtype_code(x), 0, 0)
+    sh = _stream_handle(stream)
+    ws = workspace("residuals", lib.lsefit_residuals_workspace_size(ctypes.byref(plan.plan)), dev, sh)
+    rc = lib.lsefit_residuals(ctypes.byref(b), ctypes.byref(plan.plan), _ptr(fwd["Xt"]),
+                              _ptr(fwd["map"]) if interval_given else None, _ptr(out.get("r")), _ptr(out["sse"]),
+                              _ptr(out.get("vtr")), _ptr(ws), ws.numel(), ctypes.c_void_p(sh))
+    _check(rc, "lsefit_residuals")
+    return out
+
+
+def range_batched(x, offsets, plan: BatchPlan | None = None, out=None, stream=None):
+    """Per-series [min x, max x] (lsefit_range); float64 [S, 2] on the device."""
+    dev = x.device
+    off_d = _to_device(offsets, torch.int64, dev)
+    S = off_d.numel() - 1
+    if plan is None:
+        plan = BatchPlan(offsets if not isinstance(offsets, torch.Tensor) else off_d, 1, device=dev)
+    if out is None:
+        out = torch.empty(S, 2, dtype=torch.float64, device=dev)
+    b = Batch(x.data_ptr(), None, off_d.data_ptr(), None, None, S, plan.m_max, _dtype_code(x), 0, 0)
+    sh = _stream_handle(stream)
+    nbytes = lib.lsefit_range_workspace_size(ctypes.byref(plan.plan))
+    ws = workspace("range", nbytes, dev, sh)
+    rc = lib.lsefit_range(ctypes.byref(b), ctypes.byref(plan.plan), _ptr(out), _ptr(ws), ws.numel(),
+                          ctypes.c_void_p(sh))
+    _check(rc, "lsefit_range")
     return out
 
 
@@ -460,5 +516,5 @@ def fit_differentiable(x, y, offsets, degree, interval=None, m_max=None, accum="
     if m_max is None:
         m_max = int(_to_device(degree, torch.int32, x.device).max().item())
     if plan is None:
-        plan = BatchPlan(offsets, m_max, device=x.device)
+        plan = BatchPlan(offsets, m_max, device=x.device, degree=degree)
     return LseFitFunction.apply(x, y, offsets, degree, interval, m_max, accum, plan)

@@ -30,11 +30,14 @@ def _hankel(S, m):
 
 
 def _tol(accum, m, S):
-    """1e-6 (FP64); 1e-5 for compensated FP32 at m <= 3 on a well-conditioned
-    mapped system; in general max(1e-5, cond(A_t) * 2^-24 * 4m)."""
+    """1e-6 for FP64 accumulation and 1e-5 for compensated FP32 (degree <= 3 on
+    a well-conditioned mapped system); in general the bound grows with the
+    condition of the mapped Hankel matrix: cond(A_t) * eps * 4m, with eps the
+    unit roundoff of the per-point arithmetic (2^-53 FP64, 2^-24 FP32)."""
+    cond = np.linalg.cond(_hankel(S, m))
     if accum == "f64":
-        return 1e-6
-    return max(1e-5, np.linalg.cond(_hankel(S, m)) * EPS32 * 4 * m)
+        return max(1e-6, cond * 2.0 ** -53 * 4 * m)
+    return max(1e-5, cond * EPS32 * 4 * m)
 
 
 def check_batch(L, b, res, accum, stored_x=None, stored_y=None, series=None, fp32_map=None):
@@ -78,7 +81,7 @@ def _run(L, b, accum="comp", dtype=torch.float32, tuning=None, m_max=5, with_int
     dev = torch.device("cuda")
     x = torch.from_numpy(b["x"]).to(dev).to(dtype)
     y = torch.from_numpy(b["y"]).to(dev).to(dtype)
-    plan = L.BatchPlan(b["offsets"], m_max, tuning=tuning)
+    plan = L.BatchPlan(b["offsets"], m_max, tuning=tuning, degree=b["degree"])
     res = L.fit_batched(x, y, b["offsets"], b["degree"], b["interval"] if with_interval else None,
                         m_max=m_max, accum=accum, plan=plan)
     torch.cuda.synchronize()
@@ -86,9 +89,17 @@ def _run(L, b, accum="comp", dtype=torch.float32, tuning=None, m_max=5, with_int
 
 
 @pytest.mark.parametrize("accum", ["comp", "naive", "f64"])
+def test_ragged_all_warp_tasks(L, accum):
+    b = synth.ragged_batch(num_series=300, lmin=1, lmax=70000, seed=44)
+    _, _, res, plan = _run(L, b, accum, tuning={"warp_max_len": 1 << 20})
+    assert plan.plan.n_block_tasks == 0
+    assert check_batch(L, b, res, accum) > 250
+
+
+@pytest.mark.parametrize("accum", ["comp", "naive", "f64"])
 def test_ragged_mixed_degrees(L, accum):
     b = synth.ragged_batch(num_series=400, lmin=16, lmax=40000, seed=31)
-    _, _, res, plan = _run(L, b, accum)
+    _, _, res, plan = _run(L, b, accum, tuning={"warp_max_len": 8192, "chunk_len": 65536})
     assert plan.plan.n_block_tasks > 0 and plan.plan.n_warp_tasks > 0
     assert check_batch(L, b, res, accum) > 350
 

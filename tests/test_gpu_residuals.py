@@ -1,0 +1,84 @@
+"""Parity of the residual pass (lsefit_residuals) with the oracle.
+
+SSE and V^T r are compared with the oracle's residuals of its own fit of the
+same stored points, evaluated in the mapped basis in FP64.  Tolerance: SSE
+relative 1e-4 for FP32 data (the residual r = y - f(t) is formed in FP32 and
+loses up to |y|/|r| of its 2^-24 relative precision), 1e-9 for FP64 data;
+V^T r absolute, scaled by sum_i |t_i^k| |y_i| times the same factor.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.conftest import read_golden
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import paper_1512_08017_gb300 as lib
+    return lib
+
+
+def _ref(xs, ys, m, lo, hi, fp32):
+    r = oracle.fit_interval(xs, ys, m, lo, hi, fp32=fp32)
+    t = r["s"] * (xs - r["c"])
+    res = ys - oracle.evaluate(r["Xt"], t)
+    vtr = np.array([np.sum(t ** k * res) for k in range(m + 1)])
+    scale = np.array([np.sum(np.abs(t) ** k * np.abs(ys)) for k in range(m + 1)])
+    return r, float(np.sum(res * res)), vtr, scale, res
+
+
+@pytest.mark.parametrize("dtype,accum", [(torch.float32, "comp"), (torch.float64, "f64")])
+@pytest.mark.parametrize("tuning", [None, {"warp_max_len": 256, "chunk_len": 4096}])
+def test_residuals_against_oracle(L, dtype, accum, tuning):
+    b = synth.ragged_batch(num_series=150, lmin=20, lmax=30000, seed=91)
+    xs = b["x"].astype(np.float64)
+    ys = b["y"].astype(np.float64)
+    x = torch.from_numpy(b["x"]).to(dtype).cuda()
+    y = torch.from_numpy(b["y"]).to(dtype).cuda()
+    plan = L.BatchPlan(b["offsets"], 5, tuning=tuning, degree=b["degree"])
+    fwd = L.fit_batched(x, y, b["offsets"], b["degree"], b["interval"], m_max=5, accum=accum, plan=plan)
+    out = L.residuals_batched(x, y, b["offsets"], b["degree"], fwd, want_r=True)
+    sse = out["sse"].cpu().numpy()
+    vtr = out["vtr"].cpu().numpy()
+    rr = out["r"].double().cpu().numpy()
+    tol = 1e-9 if dtype == torch.float64 else 1e-4
+    checked = 0
+    for s in range(150):
+        lo, hi = int(b["offsets"][s]), int(b["offsets"][s + 1])
+        m = int(b["degree"][s])
+        if L.status_names(fwd["status"][s: s + 1]) != ["ok"]:
+            continue
+        r, sse_ref, vtr_ref, scale, res = _ref(xs[lo:hi], ys[lo:hi], m, *b["interval"][s], fp32=accum != "f64")
+        assert abs(sse[s] - sse_ref) <= tol * sse_ref + 1e-30, (s, sse[s], sse_ref)
+        f = 8 * m * (2.0 ** -53 if accum == "f64" else 2.0 ** -24)
+        assert np.all(np.abs(vtr[s, : m + 1] - vtr_ref) <= 1e3 * f * scale + 1e-30), s
+        assert np.all(vtr[s, m + 1:] == 0.0)
+        assert np.max(np.abs(rr[lo:hi] - res)) <= 1e3 * f * (np.max(np.abs(ys[lo:hi])) + 1e-300)
+        checked += 1
+    assert checked > 120
+
+
+def test_table5_sum_of_squared_errors(L):
+    # Section III, Table I data, m = 3: the GPU's SSE of its own fit equals the
+    # exact least-squares minimum and does not exceed the paper's printed value.
+    rows, _ = read_golden("table1_sample.txt")
+    x = np.array([float(r[0]) for r in rows])
+    y = np.array([float(r[1]) for r in rows])
+    rows5, _ = read_golden("table5_fitted.txt")
+    sse_f = float(next(r[1] for r in rows5 if r[0] == "sse_f"))
+    offsets = np.array([0, 6], dtype=np.int64)
+    degree = np.array([3], dtype=np.int32)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.from_numpy(y).cuda()
+    fwd = L.fit_batched(xd, yd, offsets, degree, None, m_max=3, accum="f64")
+    out = L.residuals_batched(xd, yd, offsets, degree, fwd, interval_given=False)
+    gpu_sse = float(out["sse"].item())
+    ref = oracle.fit(x, y, 3)
+    assert abs(gpu_sse - oracle.sse(ref["X"], x, y)) <= 1e-8 * gpu_sse
+    assert gpu_sse <= sse_f
+    assert np.allclose(fwd["X"][0].cpu().numpy(), ref["X"], rtol=1e-8)

@@ -1,0 +1,91 @@
+"""Host-side schedule of the batched fit (lsefit_plan_build): no GPU needed."""
+import ctypes
+
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1512_08017_gb300 import _build
+    _build.build()
+    from paper_1512_08017_gb300 import lsefit
+    return lsefit
+
+
+def build(B, offsets, degree=None, m_max=5, **tuning):
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    S = off.size - 1
+    deg = None if degree is None else np.ascontiguousarray(degree, dtype=np.int32)
+    tun = B.Tuning()
+    for k, v in tuning.items():
+        setattr(tun, k, v)
+    plan = B.Plan()
+    dp = deg.ctypes.data_as(ctypes.c_void_p) if deg is not None else None
+    rc = B.lib.lsefit_plan_build(off.ctypes.data_as(ctypes.c_void_p), dp, S, m_max, ctypes.byref(tun), 152,
+                                 ctypes.byref(plan), None, 0, None, 0)
+    if rc not in (B.OK, B.ERR_WORKSPACE):
+        return rc, None, None, None
+    bt = np.zeros(max(4 * plan.n_block_tasks, 4), dtype=np.int32)
+    wt = np.zeros(max(4 * plan.n_warp_tasks, 4), dtype=np.int32)
+    rc = B.lib.lsefit_plan_build(off.ctypes.data_as(ctypes.c_void_p), dp, S, m_max, ctypes.byref(tun), 152,
+                                 ctypes.byref(plan), bt.ctypes.data_as(ctypes.c_void_p), plan.n_block_tasks,
+                                 wt.ctypes.data_as(ctypes.c_void_p), plan.n_warp_tasks)
+    return rc, plan, bt[: 4 * plan.n_block_tasks].reshape(-1, 4), wt[: 4 * plan.n_warp_tasks].reshape(-1, 4)
+
+
+def test_cover_and_order(B):
+    rng = np.random.default_rng(1)
+    lens = np.concatenate([[0, 1, 70000, 3], rng.integers(0, 20000, 500)])
+    off = np.concatenate([[0], np.cumsum(lens)])
+    deg = rng.integers(1, 6, lens.size)
+    rc, plan, bt, wt = build(B, off, deg, warp_max_len=4096, chunk_len=8192)
+    assert rc == B.OK
+    seen = np.zeros(lens.size, dtype=int)
+    # block tasks: consecutive chunks of one series, chunk count right, first-task index right
+    t = 0
+    while t < len(bt):
+        s, c, nch, first = bt[t]
+        assert c == 0 and first == t and nch == -(-lens[s] // 8192)
+        for k in range(nch):
+            assert tuple(bt[t + k]) == (s, k, nch, first)
+        seen[s] += 1
+        t += nch
+    assert plan.n_split_series == sum(1 for s in np.unique(bt[:, 0]) if -(-lens[s] // 8192) > 1)
+    # block tasks longest first
+    firsts = [lens[s] for s, c, _, _ in bt if c == 0]
+    assert firsts == sorted(firsts, reverse=True)
+    # warp tasks: records, grouped by degree then longest first
+    for s, lo, hi, n in wt:
+        seen[s] += 1
+        assert lens[s] <= 4096
+        assert (int(hi) << 32) + (int(lo) & 0xffffffff) == off[s] and n == lens[s]
+    keys = [(deg[s], -lens[s]) for s in wt[:, 0]]
+    assert keys == sorted(keys)
+    assert np.all(seen == 1)
+    assert plan.total_points == off[-1] and plan.num_series == lens.size
+
+
+def test_without_degrees_longest_first(B):
+    lens = np.array([5, 100, 7, 100, 3000])
+    off = np.concatenate([[0], np.cumsum(lens)])
+    rc, plan, bt, wt = build(B, off, warp_max_len=1 << 20)
+    assert rc == B.OK and plan.n_block_tasks == 0
+    assert list(wt[:, 0]) == [4, 1, 3, 2, 0]  # stable for equal lengths
+
+
+def test_bad_inputs(B):
+    assert build(B, [0, 5, 3])[0] == B.ERR_INVALID_ARG          # decreasing offsets
+    assert build(B, [1, 5])[0] == B.ERR_INVALID_ARG             # offsets[0] != 0
+    assert build(B, [0, 5], m_max=9)[0] == B.ERR_INVALID_ARG    # degree bound
+    rc, plan, _, _ = build(B, [0, 0])                            # one empty series is fine
+    assert rc == B.OK and plan.n_warp_tasks == 1
+
+
+def test_workspace_sizes(B):
+    rc, plan, _, _ = build(B, [0, 100, 200000, 200010], warp_max_len=1000, chunk_len=65536)
+    assert rc == B.OK
+    ws = B.lib.lsefit_batched_workspace_size(ctypes.byref(plan))
+    assert ws % 256 == 0 and ws >= 256 + 16 * 3
+    assert B.lib.lsefit_backward_workspace_size(ctypes.byref(plan)) > 0
+    assert B.lib.lsefit_range_workspace_size(ctypes.byref(plan)) >= 256 + 16 * 3
