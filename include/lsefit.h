@@ -154,6 +154,19 @@ int lsefit_solve(const double* sums, int64_t count, int m_sums, int m, int accum
                  const double* map, double* X, double* Xt, int32_t* status, lsefit_stream_t stream);
 
 /*
+ * lsefit_solve_cholesky -- the alternative solver Section V names as future
+ * work (a method other than Gaussian elimination): the Hankel normal matrix
+ * is symmetric positive definite for distinct abscissae (A = V^T V), so
+ * A = L L^T (Cholesky, FP64), then L w = B and L^T X = w, then the un-map.
+ * About half the arithmetic of elimination and no pivoting.  A diagonal
+ * pivot at or below (m+1) * eps * max|A| is reported as LSEFIT_ERR_SINGULAR.
+ * Arguments, layouts and statuses as for lsefit_solve.
+ */
+int lsefit_solve_cholesky(const double* sums, int64_t count, int m_sums, int m, int accum,
+                          const double* map, double* X, double* Xt, int32_t* status,
+                          lsefit_stream_t stream);
+
+/*
  * lsefit_fit -- the whole single-series fit in one launch: the streaming
  * pass of lsefit_powersums, then, in the block that completes the
  * reduction, the Gaussian elimination of Section II for every degree
@@ -228,7 +241,19 @@ typedef struct lsefit_tuning {
                                  by its block, others by the block that completes them last */
     int32_t block_threads;    /* reserved (the batched kernel runs 512 threads per block) */
     int32_t blocks_per_sm;    /* reserved (one persistent block per SM) */
-    int32_t reserved[4];
+    int32_t task_order;       /* order of the warp tasks in the plan (schedules 1 and 2):
+                                 1 = longest first; 2 (0 = default) = grouped by degree
+                                 when degrees are given, longest first within a degree */
+    int32_t schedule;         /* how warps take warp tasks:
+                                 1 = from one atomic queue, in plan order;
+                                 2 = fixed snake order (round r gives warp w task r*W + w,
+                                     or r*W + W-1-w on odd rounds; W warps in the grid);
+                                 3 (0 = default) = one queue per degree class, longest
+                                     first; every block starts on a class (blocks shared
+                                     out in proportion to the classes' points) and moves
+                                     to the next class with tasks left when its class runs
+                                     dry, so the warps of an SM run the code of one degree */
+    int32_t reserved[2];
 } lsefit_tuning;
 
 /* Host-side schedule of one batch layout (built by lsefit_plan_build).  The two
@@ -246,15 +271,21 @@ typedef struct lsefit_plan {
     int32_t num_sms;
     const int32_t* block_tasks;  /* device int32[n_block_tasks][4]: series, chunk, nchunks, first task */
     const int32_t* warp_tasks;   /* device int32[n_warp_tasks][4]: series, first point (low and
-                                    high 32 bits), length; longest first */
+                                    high 32 bits), length */
+    int32_t class_begin[LSEFIT_MAX_DEGREE + 2];  /* schedule 3: warp tasks of degree class c
+                                    (c = the degree, 0 = a degree outside 1..LSEFIT_MAX_DEGREE
+                                    or no degrees given) are [class_begin[c], class_begin[c+1]) */
+    int64_t class_points[LSEFIT_MAX_DEGREE + 1]; /* schedule 3: points of each class */
 } lsefit_plan;
 
 /*
  * lsefit_plan_build -- split a batch layout into block tasks (series longer
  * than tuning.warp_max_len, cut into chunks) and warp tasks (the shorter
- * series).  Block tasks are ordered longest first; warp tasks longest first
- * too, grouped by degree (lowest first) when degrees are given, so that the
- * warps working side by side run the same code.  Host only; no GPU needed.
+ * series).  Block tasks are ordered longest first.  Warp tasks are ordered
+ * as tuning.schedule and tuning.task_order say: by degree class and longest
+ * first within a class (schedule 3, the default), so that the warps of an SM
+ * run the code of one degree while the longest series start first.  Host
+ * only; no GPU needed.
  *  offsets_host  host int64[num_series+1] (nondecreasing, offsets[0] = 0).
  *  degree_host   host int32[num_series] or NULL (the same degrees the fits
  *                will use; only the order of the tasks depends on them).

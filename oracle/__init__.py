@@ -73,6 +73,8 @@ def _load():
         lib.orc_powersums.restype = None
         lib.orc_solve.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
         lib.orc_solve.restype = ctypes.c_int
+        lib.orc_solve_cholesky.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp]
+        lib.orc_solve_cholesky.restype = ctypes.c_int
         lib.orc_unmap.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp]
         lib.orc_unmap.restype = None
         lib.orc_fit.argtypes = [dp, dp, i64, ctypes.c_int, dp, ctypes.c_double, dp, dp, dp, dp]
@@ -134,6 +136,17 @@ def solve(S, T, m: int, eps: float = EPS64):
     T = _f64(T)
     X = np.full(m + 1, np.nan)
     st = _load().orc_solve(m, _ptr(S), _ptr(T), float(eps), _ptr(X))
+    return STATUS_NAMES[st], X
+
+
+def solve_cholesky(S, T, m: int, eps: float = EPS64):
+    """Cholesky factorisation of the Hankel normal matrix, then two triangular solves.
+
+    Returns (status_name, X)."""
+    S = _f64(S)
+    T = _f64(T)
+    X = np.full(m + 1, np.nan)
+    st = _load().orc_solve_cholesky(m, _ptr(S), _ptr(T), float(eps), _ptr(X))
     return STATUS_NAMES[st], X
 
 

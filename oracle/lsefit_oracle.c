@@ -162,6 +162,55 @@ int orc_solve(int m, const double* S, const double* T, double eps, double* X)
     return orc_gauss_inplace(m, A, B, X, eps);
 }
 
+/*
+ * Alternative solver (Section V names methods other than Gaussian
+ * elimination as future work): A = S_{j+k} is symmetric and, for distinct
+ * abscissae, positive definite (A = V^T V), so A = L L^T with L lower
+ * triangular (Cholesky), then L z = B and L^T X = z.  A diagonal pivot
+ * d_kk = A_kk - sum_j L_kj^2 at or below (m+1)*eps*max|A| means A is not
+ * numerically positive definite: reported as singular.
+ */
+int orc_solve_cholesky(int m, const double* S, const double* T, double eps, double* X)
+{
+    if (m < 1 || m > ORC_MAX_M) return ORC_BAD_ARG;
+    const int N = m + 1;
+    for (int k = 0; k <= 2 * m; ++k)
+        if (!isfinite(S[k])) return ORC_NONFINITE;
+    for (int k = 0; k <= m; ++k)
+        if (!isfinite(T[k])) return ORC_NONFINITE;
+    double Lm[(ORC_MAX_M + 1) * (ORC_MAX_M + 1)];
+    double amax = 0.0;
+    for (int k = 0; k <= 2 * m; ++k)
+        if (fabs(S[k]) > amax) amax = fabs(S[k]);
+    const double tol = (double)N * eps * amax;
+    for (int j = 0; j < N; ++j) {
+        double d = S[2 * j];
+        for (int k = 0; k < j; ++k) d -= Lm[j * N + k] * Lm[j * N + k];
+        if (!(d > tol)) return ORC_SINGULAR;
+        const double ljj = sqrt(d);
+        Lm[j * N + j] = ljj;
+        for (int i = j + 1; i < N; ++i) {
+            double v = S[i + j];
+            for (int k = 0; k < j; ++k) v -= Lm[i * N + k] * Lm[j * N + k];
+            Lm[i * N + j] = v / ljj;
+        }
+    }
+    double z[ORC_MAX_M + 1];
+    for (int i = 0; i < N; ++i) {
+        double acc = T[i];
+        for (int k = 0; k < i; ++k) acc -= Lm[i * N + k] * z[k];
+        z[i] = acc / Lm[i * N + i];
+    }
+    for (int i = N - 1; i >= 0; --i) {
+        double acc = z[i];
+        for (int k = i + 1; k < N; ++k) acc -= Lm[k * N + i] * X[k];
+        X[i] = acc / Lm[i * N + i];
+    }
+    for (int i = 0; i < N; ++i)
+        if (!isfinite(X[i])) return ORC_SINGULAR;
+    return ORC_OK;
+}
+
 /* Binomial coefficient C(k, j) as a double (exact for k <= 16). */
 static double orc_binom(int k, int j)
 {

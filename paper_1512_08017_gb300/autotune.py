@@ -22,10 +22,9 @@ import torch
 from . import lsefit as L
 
 DEFAULT_CANDIDATES = [
-    {"warp_max_len": wm, "chunk_len": ch}
-    for wm in (4096, 65536, 1 << 20)
-    for ch in (65536, 262144)
-] + [{"warp_max_len": 1024, "chunk_len": 16384}]
+    {"warp_max_len": 1 << 20, "schedule": sched} for sched in (1, 2, 3)
+] + [{"warp_max_len": wm, "chunk_len": ch, "schedule": 3}
+     for wm in (4096, 65536) for ch in (65536, 262144)]
 
 _lock = threading.Lock()
 

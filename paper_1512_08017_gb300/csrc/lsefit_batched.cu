@@ -33,6 +33,8 @@ static void resolve_tuning(const lsefit_tuning* in, lsefit_tuning* out) {
     if (t.chunk_len < 1024) t.chunk_len = 1024;
     t.block_threads = kBBlock;
     t.blocks_per_sm = 1;
+    if (t.task_order < 1 || t.task_order > 2) t.task_order = 2;
+    if (t.schedule < 1 || t.schedule > 3) t.schedule = 3;
     *out = t;
 }
 
@@ -83,15 +85,36 @@ extern "C" int lsefit_plan_build(const int64_t* offsets, const int32_t* degree, 
     auto len_of = [&](int32_t s) { return offsets[s + 1] - offsets[s]; };
     auto longer = [&](int32_t a, int32_t b) { return len_of(a) > len_of(b); };
     std::stable_sort(longs.begin(), longs.end(), longer);
-    if (degree != nullptr) {
-        // group the warp tasks by degree (the warps of an SM then run the same
-        // code at the same time), longest first within a degree
+    const int order = plan->tuning.task_order;
+    auto cls_of = [&](int32_t s) {
+        if (degree == nullptr) return 0;
+        const int d = degree[s];
+        return d >= 1 && d <= LSEFIT_MAX_DEGREE ? d : 0;
+    };
+    if (plan->tuning.schedule == 3) {
+        // degree classes (invalid degrees first), longest first within a class
+        auto by_class = [&](int32_t a, int32_t b) {
+            const int ca = cls_of(a), cb = cls_of(b);
+            return ca != cb ? ca < cb : len_of(a) > len_of(b);
+        };
+        std::stable_sort(shorts.begin(), shorts.end(), by_class);
+    } else if (degree != nullptr && order == 2) {
+        // grouped by degree (warps side by side run the same code), longest first within
         auto by_degree = [&](int32_t a, int32_t b) {
             return degree[a] != degree[b] ? degree[a] < degree[b] : len_of(a) > len_of(b);
         };
         std::stable_sort(shorts.begin(), shorts.end(), by_degree);
     } else {
         std::stable_sort(shorts.begin(), shorts.end(), longer);
+    }
+    {
+        int32_t count[LSEFIT_MAX_DEGREE + 1] = {};
+        for (int32_t s : shorts) {
+            ++count[cls_of(s)];
+            plan->class_points[cls_of(s)] += len_of(s);
+        }
+        plan->class_begin[0] = 0;
+        for (int c = 0; c <= LSEFIT_MAX_DEGREE; ++c) plan->class_begin[c + 1] = plan->class_begin[c] + count[c];
     }
     int64_t t = 0;
     for (int32_t s : longs) {
@@ -117,6 +140,7 @@ extern "C" int lsefit_plan_build(const int64_t* offsets, const int32_t* degree, 
 
 // Workspace: queue counters | tickets [nbt] | FP64 chunk partials [nbt][3m_max+1]
 // | prepared map constants [num_series] (16 bytes each).
+static_assert(kCounters * sizeof(unsigned) <= kAlign, "queue counters fit the first workspace slot");
 static size_t ws_tickets_off() { return kAlign; }
 static size_t ws_partials_off(const lsefit_plan* plan) {
     return ws_tickets_off() + align_up((size_t)plan->n_block_tasks * sizeof(unsigned), kAlign);
@@ -174,6 +198,9 @@ extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* 
     p.warp_tasks = reinterpret_cast<const int4*>(plan->warp_tasks);
     p.n_warp_tasks = plan->n_warp_tasks;
     p.total_points = plan->total_points;
+    p.sched = plan->tuning.schedule;
+    for (int c = 0; c <= kClasses; ++c) p.cls_begin[c] = plan->class_begin[c];
+    for (int c = 0; c < kClasses; ++c) p.cls_points[c] = plan->class_points[c];
     p.X = X;
     p.Xt = Xt;
     p.sums = sums;
@@ -214,7 +241,7 @@ extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* 
     if (grid < 1) grid = 1;
     {
         const int pt = 256;
-        const int64_t items = std::max<int64_t>(std::max<int64_t>(b.num_series, plan->n_block_tasks), 3);
+        const int64_t items = std::max<int64_t>(std::max<int64_t>(b.num_series, plan->n_block_tasks), kCounters);
         const int64_t pb = (items + pt - 1) / pt;
         auto prep = b.accum == LSEFIT_ACCUM_F64 ? batched_prep_kernel<false> : batched_prep_kernel<true>;
         prep<<<(unsigned)pb, pt, 0, (cudaStream_t)stream>>>(p);

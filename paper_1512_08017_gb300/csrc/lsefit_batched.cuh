@@ -11,10 +11,10 @@
 //     series.
 // Persistent blocks (one per SM: the warp rings take most of its shared
 // memory) take block tasks from an atomic queue until it is
-// empty.  Then every warp works through warp tasks in a fixed snake order
-// (round r gives warp w task r*W + w, or r*W + W-1-w on odd rounds, W warps
-// in the grid): with the tasks sorted longest first this balances the warps
-// and lets each one prefetch its next tasks' records.  A warp streams its
+// empty.  Then every warp takes warp tasks from a second atomic queue, in
+// plan order (longest first, grouped by degree when the plan had degrees),
+// drawing each index three tasks ahead so that its record, degree and map
+// constants are loaded before they are needed.  A warp streams its
 // series through a ring of shared-memory stages filled by cp.async copies
 // that run ahead across task boundaries, so the bytes in flight do not
 // depend on registers or on the length of the current series.
@@ -40,6 +40,9 @@ constexpr int kBWarps = kBBlock / 32;
 constexpr int kDefaultWarpMaxLen = 65536;
 constexpr int kDefaultChunkLen = 65536;
 
+constexpr int kClasses = LSEFIT_MAX_DEGREE + 1;  // degree classes of the warp tasks
+constexpr int kCounters = 3 + kClasses;          // queue counters in the workspace
+
 struct BParams {
     const void* x;
     const void* y;
@@ -53,6 +56,9 @@ struct BParams {
     const int4* warp_tasks;   // {series, first point (low, high 32 bits), length}
     int n_warp_tasks;
     int64_t total_points;
+    int sched;             // 1 one queue, 2 snake order, 3 degree classes
+    int cls_begin[LSEFIT_MAX_DEGREE + 2];        // warp tasks of class c: [cls_begin[c], cls_begin[c+1])
+    long long cls_points[LSEFIT_MAX_DEGREE + 1];  // points of class c
     double* X;
     double* Xt;
     double* sums;
@@ -61,7 +67,7 @@ struct BParams {
     double eps;            // singularity threshold epsilon of the accumulation
     double* partials;      // [n_block_tasks][3*m_max+1]
     unsigned* tickets;     // [n_block_tasks], slot of a split series = its first task
-    unsigned* counters;    // [0] block queue, [1] warp queue, [2] exited blocks
+    unsigned* counters;    // [0] block queue, [1] warp queue, [2] exited blocks, [3 + c] class c queue
     double2* mapc;         // [num_series]: FP32 paths {float2(c, s), unused}; FP64 {c, s}
     unsigned char* pend;   // [grid * kBWarps] queues of finished series
 };
@@ -75,7 +81,7 @@ struct BParams {
 template <bool FP32MAP>
 __global__ void batched_prep_kernel(BParams p) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < 3) p.counters[s] = 0u;
+    if (s < kCounters) p.counters[s] = 0u;
     if (s < p.n_block_tasks) p.tickets[s] = 0u;
     if (s >= p.num_series) return;
     double c, sc;
@@ -158,6 +164,13 @@ constexpr int kRing = 3;                         // stages per warp ring
 constexpr int kStageBytes = 2048;                // bytes of x (and of y) per stage
 constexpr int kStageVecs = kStageBytes / 16;     // 16-byte vectors per stage (4 per lane)
 constexpr int kFoldStages = 2;                   // compensated batch = this many stages
+#ifndef LSEFIT_STAGE_UNROLL
+#define LSEFIT_STAGE_UNROLL 1
+#endif
+// Vectors of a stage a lane handles per loop iteration.  Kept small: every
+// degree has its own copy of the loop, and the warps of an SM that work on
+// different degrees share its instruction caches.
+constexpr int kStageUnroll = LSEFIT_STAGE_UNROLL;
 constexpr int kBlockUnroll = 2;                  // vectors in flight per thread in block tasks
 
 struct __align__(16) StageRec {
@@ -197,11 +210,18 @@ struct Ring {
     }
 };
 
-// Producer cursor of a warp (registers, identical in all lanes).  Two task
-// records are prefetched ahead: `b` has its degree and map loaded too, `a`
-// only its record, so no load on the issue path waits for another.
+// Producer cursor of a warp.  Warp tasks come from one atomic queue in plan
+// order (warps that drew long series simply take fewer), from a fixed snake
+// order (round r gives warp w task r*W + w, or r*W + W-1-w on odd rounds, W
+// warps in the grid), or from one queue per degree class: a block starts on
+// the class its index falls in when the blocks are shared out in proportion
+// to the classes' points, and a warp whose class has run dry moves on to the
+// next class with tasks left, so the warps of an SM keep running the code of
+// one degree.  Three tasks are in the pipeline ahead of the one being issued,
+// one step per advance, so no advance waits on a load: tq (lane 0) holds the
+// next index, a (lane 0) the task record loaded for the index before, b (all
+// lanes) a record with its degree and map constants loaded.
 struct Cursor {
-    int round, wid, nw;
     bool have;
     int s, deg;
     long long pos, end;
@@ -211,38 +231,101 @@ struct Cursor {
     int4 brec;
     int bdeg;
     double2 bmap;
-    bool av;
-    int4 arec;
+    int at;     // lane 0: task index of slot a (>= n_warp_tasks: none)
+    int4 arec;  // lane 0: record of slot a
+    int tq;     // lane 0: next task index
+    int round;  // lane 0: snake round of the next index
+    int cls;    // lane 0: degree class drawn from
 };
 
-__device__ __forceinline__ void cursor_fetch_record(Cursor& cu, const BParams& p) {
-    const long long t =
-        (long long)cu.round * cu.nw + ((cu.round & 1) ? (cu.nw - 1 - cu.wid) : cu.wid);
-    cu.round++;
-    cu.av = t < p.n_warp_tasks;
-    if (cu.av) cu.arec = p.warp_tasks[t];
+__device__ __forceinline__ int cursor_draw(Cursor& cu, const BParams& p) {
+    constexpr int kNone = 0x7fffffff;
+    if (p.sched == 2) {
+        const long long nw = (long long)gridDim.x * kBWarps;
+        const long long wid = (long long)blockIdx.x * kBWarps + (threadIdx.x >> 5);
+        const long long t = (long long)cu.round * nw + ((cu.round & 1) ? (nw - 1 - wid) : wid);
+        cu.round++;
+        return t < p.n_warp_tasks ? (int)t : kNone;
+    }
+    if (p.sched != 3) return (int)atomicAdd(&p.counters[1], 1u);
+    // every class is tried at most once; a class stays behind once it runs dry
+    for (int tries = 0; tries < kClasses; ++tries) {
+        const int c = cu.cls;
+        const int b = p.cls_begin[c], n = p.cls_begin[c + 1] - b;
+        if (n > 0) {
+            const unsigned k = atomicAdd(&p.counters[3 + c], 1u);
+            if (k < (unsigned)n) return b + (int)k;
+        }
+        cu.cls = c + 1 == kClasses ? 0 : c + 1;
+    }
+    return kNone;
 }
 
-// Make task b current, move a into b (loading its degree and map) and fetch a
-// new record into a.  Tasks of an invalid degree are marked and skipped.
+// First class of a block: blocks shared out over the classes in proportion
+// to their points.
+__device__ __forceinline__ int first_class(const BParams& p) {
+    long long total = 0;
+    for (int c = 0; c < kClasses; ++c) total += p.cls_points[c];
+    if (total <= 0) return 0;
+    const double target = ((double)blockIdx.x + 0.5) / (double)gridDim.x * (double)total;
+    long long cum = 0;
+    for (int c = 0; c < kClasses; ++c) {
+        cum += p.cls_points[c];
+        if ((double)cum > target) return c;
+    }
+    return kClasses - 1;
+}
+
+__device__ __forceinline__ void cursor_init(Cursor& cu, const BParams& p) {
+    cu.have = false;
+    cu.bv = false;
+    cu.at = 0x7fffffff;
+    cu.arec = make_int4(0, 0, 0, 0);
+    cu.tq = 0x7fffffff;
+    cu.round = 0;
+    cu.cls = 0;
+    if ((threadIdx.x & 31) == 0) {
+        if (p.sched == 3) cu.cls = first_class(p);
+        cu.tq = cursor_draw(cu, p);
+    }
+}
+
+// One step of the pipeline: b becomes current, a moves to b (loading degree
+// and map), the queued index moves to a (loading its record), and a new
+// index is drawn.  Tasks of an invalid degree are marked and skipped.
+__device__ __forceinline__ void cursor_step(Cursor& cu, const BParams& p) {
+    const int lane = threadIdx.x & 31;
+    cu.have = cu.bv;
+    if (cu.have) {
+        cu.s = cu.brec.x;
+        cu.pos = ((long long)(unsigned)cu.brec.z << 32) | (unsigned)cu.brec.y;
+        cu.end = cu.pos + cu.brec.w;
+        cu.deg = cu.bdeg;
+        cu.map = cu.bmap;
+        cu.first = true;
+    }
+    const int at = __shfl_sync(0xffffffffu, cu.at, 0);
+    cu.bv = at < p.n_warp_tasks;
+    if (cu.bv) {
+        cu.brec.x = __shfl_sync(0xffffffffu, cu.arec.x, 0);
+        cu.brec.y = __shfl_sync(0xffffffffu, cu.arec.y, 0);
+        cu.brec.z = __shfl_sync(0xffffffffu, cu.arec.z, 0);
+        cu.brec.w = __shfl_sync(0xffffffffu, cu.arec.w, 0);
+        cu.bdeg = p.degree[cu.brec.x];
+        cu.bmap = p.mapc[cu.brec.x];
+    }
+    if (lane == 0) {
+        cu.at = cu.tq;
+        if (cu.tq < p.n_warp_tasks) {
+            cu.arec = p.warp_tasks[cu.tq];
+            cu.tq = cursor_draw(cu, p);
+        }
+    }
+}
+
 __device__ __forceinline__ void cursor_advance(Cursor& cu, const BParams& p) {
     for (;;) {
-        cu.have = cu.bv;
-        if (cu.have) {
-            cu.s = cu.brec.x;
-            cu.pos = ((long long)(unsigned)cu.brec.z << 32) | (unsigned)cu.brec.y;
-            cu.end = cu.pos + cu.brec.w;
-            cu.deg = cu.bdeg;
-            cu.map = cu.bmap;
-            cu.first = true;
-        }
-        cu.bv = cu.av;
-        if (cu.bv) {
-            cu.brec = cu.arec;
-            cu.bdeg = p.degree[cu.arec.x];
-            cu.bmap = p.mapc[cu.arec.x];
-            cursor_fetch_record(cu, p);
-        }
+        cursor_step(cu, p);
         if (!cu.have || (cu.deg >= 1 && cu.deg <= p.m_max)) return;
         // not fitted at all: status and NaN row, no stages
         if ((threadIdx.x & 31) == 0) {
@@ -505,6 +588,22 @@ __device__ void block_task(const BParams& p, int t, int4 task, dflt* red, double
 // g0 + j (g0: r0 rounded down to a 16-byte vector); points outside
 // [r0, r0 + n) are masked out.
 // ---------------------------------------------------------------------------
+// Zero the pair (t, y) where its element index e (first of the pair) is
+// outside [lo, hi): a zero abscissa and ordinate add nothing to the sums of
+// degree >= 1 (S_0 is the count, kept apart).
+__device__ __forceinline__ void mask_pair(u64& t, u64& y, int e, int lo, int hi) {
+    float t0, t1, y0, y1;
+    up2(t, t0, t1);
+    up2(y, y0, y1);
+    const bool ok0 = e >= lo && e < hi, ok1 = e + 1 >= lo && e + 1 < hi;
+    t = pk2(ok0 ? t0 : 0.0f, ok1 ? t1 : 0.0f);
+    y = pk2(ok0 ? y0 : 0.0f, ok1 ? y1 : 0.0f);
+}
+
+// Accumulate the points [lo, hi) of one landed stage (element indices
+// relative to the stage's first vector).  Full vectors and the partial first
+// and last vectors of a series take the same packed code; a partial vector
+// only masks its pairs.
 template <int M, int DT, bool COMP, bool SHL>
 __device__ __forceinline__ void stage_accumulate_f32(AccF32<M, COMP, SHL>& A, const unsigned char* xb,
                                                      const unsigned char* yb, long long r0, int n, float cf,
@@ -516,38 +615,29 @@ __device__ __forceinline__ void stage_accumulate_f32(AccF32<M, COMP, SHL>& A, co
     const int nv = (hi + PV - 1) / PV;
     const u64 c2 = pk2(cf, cf), s2 = pk2(sf, sf);
     const bool full = (lo == 0 && n == P);
-#pragma unroll
+#pragma unroll kStageUnroll
     for (int q = 0; q < kStageVecs / 32; ++q) {
         const int v = lane + 32 * q;
-        if (v >= nv) continue;
+        if (v >= nv) break;
         const uint4 xv = *reinterpret_cast<const uint4*>(xb + 16 * v);
         const uint4 yv = *reinterpret_cast<const uint4*>(yb + 16 * v);
-        if (full || (v * PV >= lo && (v + 1) * PV <= hi)) {
-            feed_vec<M, DT, COMP, true, false, SHL>(A, xv, yv, c2, s2);
-        } else {
-            float xs[PV], ys[PV];
+        const bool part = !full && (v * PV < lo || (v + 1) * PV > hi);
+        const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
+        const uint32_t yw[4] = {yv.x, yv.y, yv.z, yv.w};
+        constexpr int NPAIR = PV / 2;
+#pragma unroll
+        for (int k = 0; k < NPAIR; ++k) {
+            u64 tp, yp;
             if (DT == LSEFIT_F32) {
-                xs[0] = __uint_as_float(xv.x); xs[1] = __uint_as_float(xv.y);
-                xs[2 % PV] = __uint_as_float(xv.z); xs[3 % PV] = __uint_as_float(xv.w);
-                ys[0] = __uint_as_float(yv.x); ys[1] = __uint_as_float(yv.y);
-                ys[2 % PV] = __uint_as_float(yv.z); ys[3 % PV] = __uint_as_float(yv.w);
+                tp = pk2(__uint_as_float(xw[2 * k]), __uint_as_float(xw[2 * k + 1]));
+                yp = pk2(__uint_as_float(yw[2 * k]), __uint_as_float(yw[2 * k + 1]));
             } else {
-                const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
-                const uint32_t yw[4] = {yv.x, yv.y, yv.z, yv.w};
-#pragma unroll
-                for (int k = 0; k < PV / 2; ++k) {
-                    xs[2 * k] = bf16_lo(xw[k]); xs[2 * k + 1] = bf16_hi(xw[k]);
-                    ys[2 * k] = bf16_lo(yw[k]); ys[2 * k + 1] = bf16_hi(yw[k]);
-                }
+                tp = pk2(bf16_lo(xw[k]), bf16_hi(xw[k]));
+                yp = pk2(bf16_lo(yw[k]), bf16_hi(yw[k]));
             }
-#pragma unroll
-            for (int k = 0; k < PV; k += 2) {
-                const int e0 = v * PV + k, e1 = e0 + 1;
-                const bool ok0 = e0 >= lo && e0 < hi, ok1 = e1 >= lo && e1 < hi;
-                const float t0 = ok0 ? __fmul_rn(__fsub_rn(xs[k], cf), sf) : 0.0f;
-                const float t1 = ok1 ? __fmul_rn(__fsub_rn(xs[k + 1], cf), sf) : 0.0f;
-                A.template add_pair<false>(pk2(t0, t1), pk2(ok0 ? ys[k] : 0.0f, ok1 ? ys[k + 1] : 0.0f));
-            }
+            tp = mul2(sub2(tp, c2), s2);
+            if (part) mask_pair(tp, yp, v * PV + 2 * k, lo, hi);
+            A.template add_pair<false>(tp, yp);
         }
     }
 }
@@ -742,13 +832,9 @@ __global__ void __launch_bounds__(kBBlock, 1) batched_kernel(BParams p) {
         Ring R;
         R.bind(smem + warp * kRingWarpBytes);
         Cursor cu;
-        cu.wid = blockIdx.x * kBWarps + warp;
-        cu.nw = gridDim.x * kBWarps;
-        cu.round = 0;
-        cu.have = false;
-        cu.bv = false;
-        cursor_fetch_record(cu, p);
-        cursor_advance(cu, p);  // a -> b
+        cursor_init(cu, p);
+        cursor_step(cu, p);     // index -> a
+        cursor_step(cu, p);     // a -> b
         cursor_advance(cu, p);  // b -> current
         int pending = 0;
 #pragma unroll
@@ -779,9 +865,7 @@ __global__ void __launch_bounds__(kBBlock, 1) batched_kernel(BParams p) {
     if (tid == 0) {
         __threadfence();
         if (atomicAdd(&p.counters[2], 1u) == gridDim.x - 1) {
-            p.counters[0] = 0u;
-            p.counters[1] = 0u;
-            p.counters[2] = 0u;
+            for (int c = 0; c < kCounters; ++c) p.counters[c] = 0u;
         }
     }
 }

@@ -572,6 +572,63 @@ __device__ __forceinline__ int hankel_ge(int m, const double* S, const double* r
     return st;
 }
 
+// Cholesky factorisation of the padded system (the Hankel matrix is
+// symmetric positive definite for distinct abscissae): A = L L^T, then
+// L w = rhs and L^T z = w.  A diagonal pivot at or below (m+1) * eps * max|A|
+// is singular.  The padded identity block factors to itself.
+template <int NMAX>
+__device__ __forceinline__ int hankel_cholesky(int m, const double* S, const double* rhs, double* z, double eps) {
+    constexpr int N = NMAX + 1;
+    double amax = 0.0;
+#pragma unroll
+    for (int k = 0; k <= 2 * NMAX; ++k)
+        if (k <= 2 * m) amax = fmax(amax, fabs(S[k]));
+    const double tol = (double)(m + 1) * eps * amax;
+    double Lm[N][N];
+    double inv[N];
+    int st = LSEFIT_OK;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        double d = (j <= m) ? S[2 * j] : 1.0;
+#pragma unroll
+        for (int k = 0; k < j; ++k) d = fma(-Lm[j][k], Lm[j][k], d);
+        if (j <= m && !(d > tol)) st = LSEFIT_ERR_SINGULAR;
+        const double ljj = sqrt(fmax(d, 0.0));
+        Lm[j][j] = ljj;
+        inv[j] = 1.0 / ljj;
+#pragma unroll
+        for (int i = j + 1; i < N; ++i) {
+            double v = (i <= m && j <= m) ? S[i + j] : 0.0;
+#pragma unroll
+            for (int k = 0; k < j; ++k) v = fma(-Lm[i][k], Lm[j][k], v);
+            Lm[i][j] = v * inv[j];
+        }
+    }
+    double w[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        double acc = (i <= m) ? rhs[i] : 0.0;
+#pragma unroll
+        for (int k = 0; k < i; ++k) acc = fma(-Lm[i][k], w[k], acc);
+        w[i] = acc * inv[i];
+    }
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+        double acc = w[i];
+#pragma unroll
+        for (int k = i + 1; k < N; ++k) acc = fma(-Lm[k][i], z[k], acc);
+        z[i] = acc * inv[i];
+    }
+    if (st == LSEFIT_OK) {
+        bool zf = true;
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (i <= m) zf = zf && isfinite(z[i]);
+        if (!zf) st = LSEFIT_ERR_SINGULAR;
+    }
+    return st;
+}
+
 // Checks that precede the elimination: interval, point count, finiteness.
 __device__ __forceinline__ int fit_precheck(int m, const double* S, const double* T, bool map_ok) {
     if (!map_ok) return LSEFIT_ERR_BAD_INTERVAL;
@@ -582,13 +639,13 @@ __device__ __forceinline__ int fit_precheck(int m, const double* S, const double
     return fin ? LSEFIT_OK : LSEFIT_ERR_NONFINITE;
 }
 
-template <int NMAX>
+template <int NMAX, bool CHOL = false>
 __device__ int solve_hankel_rt(int m, const double* S, const double* T, double c, double s,
                                bool map_ok, double eps, double* Xt, double* X, int ncoef) {
     constexpr int N = NMAX + 1;
     double z[N];
     int st = fit_precheck(m, S, T, map_ok);
-    if (st == LSEFIT_OK) st = hankel_ge<NMAX>(m, S, T, z, eps);
+    if (st == LSEFIT_OK) st = CHOL ? hankel_cholesky<NMAX>(m, S, T, z, eps) : hankel_ge<NMAX>(m, S, T, z, eps);
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
     if (st != LSEFIT_OK) {
         for (int i = 0; i < ncoef; ++i) {

@@ -8,7 +8,7 @@ namespace lsefit {
 
 // One system per thread.  Systems of every degree up to NMAX share the
 // padded elimination, so a warp never diverges on the degree.
-template <int NMAX>
+template <int NMAX, bool CHOL>
 __global__ void solve_kernel(const double* sums, int64_t count, int m_sums, int m, double eps,
                              const double* map, double* X, double* Xt, int32_t* status) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -21,7 +21,7 @@ __global__ void solve_kernel(const double* sums, int64_t count, int m_sums, int 
         s = map[2 * i + 1];
         ok = isfinite(c) && isfinite(s) && s != 0.0;
     }
-    const int st = solve_hankel_rt<NMAX>(m, row, row + 2 * m_sums + 1, c, s, ok, eps,
+    const int st = solve_hankel_rt<NMAX, CHOL>(m, row, row + 2 * m_sums + 1, c, s, ok, eps,
                                          Xt ? Xt + i * (m + 1) : nullptr, X + i * (m + 1), m + 1);
     if (status) status[i] = st;
 }
@@ -30,9 +30,8 @@ __global__ void solve_kernel(const double* sums, int64_t count, int m_sums, int 
 
 using namespace lsefit;
 
-extern "C" int lsefit_solve(const double* sums, int64_t count, int m_sums, int m, int accum,
-                            const double* map, double* X, double* Xt, int32_t* status,
-                            lsefit_stream_t stream) {
+static int launch_solve(bool chol, const double* sums, int64_t count, int m_sums, int m, int accum,
+                        const double* map, double* X, double* Xt, int32_t* status, lsefit_stream_t stream) {
     if (count < 0 || m < 1 || m > LSEFIT_MAX_DEGREE || m_sums < m || m_sums > LSEFIT_MAX_DEGREE)
         return LSEFIT_ERR_INVALID_ARG;
     if (accum < LSEFIT_ACCUM_NAIVE || accum > LSEFIT_ACCUM_F64) return LSEFIT_ERR_INVALID_ARG;
@@ -41,9 +40,25 @@ extern "C" int lsefit_solve(const double* sums, int64_t count, int m_sums, int m
     const int threads = 64;
     const int64_t blocks = (count + threads - 1) / threads;
     if (blocks > 0x7fffffffll) return LSEFIT_ERR_INVALID_ARG;
-    auto k = m <= 1 ? solve_kernel<1> : m == 2 ? solve_kernel<2> : m == 3 ? solve_kernel<3>
-           : m <= 5 ? solve_kernel<5> : solve_kernel<8>;
+    typedef void (*kern_t)(const double*, int64_t, int, int, double, const double*, double*, double*, int32_t*);
+    kern_t k;
+    if (chol) k = m <= 1 ? solve_kernel<1, true> : m == 2 ? solve_kernel<2, true> : m == 3 ? solve_kernel<3, true>
+                : m <= 5 ? solve_kernel<5, true> : solve_kernel<8, true>;
+    else k = m <= 1 ? solve_kernel<1, false> : m == 2 ? solve_kernel<2, false> : m == 3 ? solve_kernel<3, false>
+             : m <= 5 ? solve_kernel<5, false> : solve_kernel<8, false>;
     k<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(sums, count, m_sums, m, singular_eps(accum), map,
                                                               X, Xt, status);
     return cudaGetLastError() == cudaSuccess ? LSEFIT_OK : LSEFIT_ERR_CUDA;
+}
+
+extern "C" int lsefit_solve(const double* sums, int64_t count, int m_sums, int m, int accum,
+                            const double* map, double* X, double* Xt, int32_t* status,
+                            lsefit_stream_t stream) {
+    return launch_solve(false, sums, count, m_sums, m, accum, map, X, Xt, status, stream);
+}
+
+extern "C" int lsefit_solve_cholesky(const double* sums, int64_t count, int m_sums, int m, int accum,
+                                     const double* map, double* X, double* Xt, int32_t* status,
+                                     lsefit_stream_t stream) {
+    return launch_solve(true, sums, count, m_sums, m, accum, map, X, Xt, status, stream);
 }

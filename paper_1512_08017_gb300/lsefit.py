@@ -40,7 +40,7 @@ MAX_DEGREE = 8
 
 # per-fit status names (same vocabulary as the oracle's)
 STATUS_NAMES = {OK: "ok", ERR_N_TOO_SMALL: "n_too_small", ERR_SINGULAR: "singular",
-                ERR_NONFINITE: "nonfinite", ERR_BAD_INTERVAL: "bad_interval"}
+                ERR_NONFINITE: "nonfinite", ERR_BAD_INTERVAL: "bad_interval", ERR_INVALID_ARG: "invalid_arg"}
 
 _DTYPES = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
 
@@ -64,7 +64,8 @@ class Batch(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("warp_max_len", ctypes.c_int32), ("chunk_len", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("task_order", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class Plan(ctypes.Structure):
@@ -72,7 +73,9 @@ class Plan(ctypes.Structure):
                 ("n_block_tasks", ctypes.c_int32), ("n_warp_tasks", ctypes.c_int32),
                 ("n_split_series", ctypes.c_int32), ("m_max", ctypes.c_int32),
                 ("tuning", Tuning), ("grid", ctypes.c_int32), ("num_sms", ctypes.c_int32),
-                ("block_tasks", ctypes.c_void_p), ("warp_tasks", ctypes.c_void_p)]
+                ("block_tasks", ctypes.c_void_p), ("warp_tasks", ctypes.c_void_p),
+                ("class_begin", ctypes.c_int32 * (MAX_DEGREE + 2)),
+                ("class_points", ctypes.c_int64 * (MAX_DEGREE + 1))]
 
 
 # (name, restype, argtypes) of every symbol include/lsefit.h declares
@@ -84,6 +87,7 @@ SIGNATURES = {
     "lsefit_powersums_workspace_size": (_SZ, [_INT]),
     "lsefit_powersums": (_INT, [_VP, _VP, _I64, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "lsefit_solve": (_INT, [_VP, _I64, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP]),
+    "lsefit_solve_cholesky": (_INT, [_VP, _I64, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP]),
     "lsefit_fit": (_INT, [_VP, _VP, _I64, _INT, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "lsefit_fit_noalloc_scratch_bytes": (_SZ, []),
     "lsefit_fit_noalloc": (_INT, [_VP, _VP, _I64, _INT, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -224,7 +228,7 @@ def powersums(x: torch.Tensor, y: torch.Tensor, m: int, accum="comp", interval=N
 
 
 def solve(sums: torch.Tensor, m: int, m_sums: int | None = None, map=None, accum="comp", *, X=None, Xt=None,
-          status=None, stream=None):
+          status=None, stream=None, method="gauss"):
     """Gaussian elimination of the normal equations (lsefit_solve).
 
     sums: [count, 3*m_sums+2] or [3*m_sums+2] float64 CUDA tensor; accum: the
@@ -244,8 +248,11 @@ def solve(sums: torch.Tensor, m: int, m_sums: int | None = None, map=None, accum
         Xt = torch.empty(count, m + 1, dtype=torch.float64, device=dev)
     if status is None:
         status = torch.empty(count, dtype=torch.int32, device=dev)
-    rc = lib.lsefit_solve(_ptr(S), count, int(m_sums), int(m), _accum_code(accum), _ptr(map), _ptr(X),
-                          _ptr(Xt), _ptr(status), ctypes.c_void_p(_stream_handle(stream)))
+    fn = lib.lsefit_solve if method == "gauss" else lib.lsefit_solve_cholesky
+    if method not in ("gauss", "cholesky"):
+        raise ValueError("method is 'gauss' or 'cholesky'")
+    rc = fn(_ptr(S), count, int(m_sums), int(m), _accum_code(accum), _ptr(map), _ptr(X),
+            _ptr(Xt), _ptr(status), ctypes.c_void_p(_stream_handle(stream)))
     _check(rc, "lsefit_solve")
     if single:
         return X.reshape(-1), Xt.reshape(-1), status
@@ -351,7 +358,8 @@ class BatchPlan:
     def tuning(self) -> dict:
         t = self.plan.tuning
         return {"warp_max_len": t.warp_max_len, "chunk_len": t.chunk_len,
-                "block_threads": t.block_threads, "blocks_per_sm": t.blocks_per_sm}
+                "block_threads": t.block_threads, "blocks_per_sm": t.blocks_per_sm, "task_order": t.task_order,
+                "schedule": t.schedule}
 
 
 def _to_device(a, dtype, device):

@@ -106,7 +106,11 @@ def test_ragged_mixed_degrees(L, accum):
 
 @pytest.mark.parametrize("tuning", [{"warp_max_len": 64, "chunk_len": 1024},
                                     {"warp_max_len": 1 << 20},
-                                    {"warp_max_len": 16, "chunk_len": 4096, "blocks_per_sm": 1}])
+                                    {"warp_max_len": 16, "chunk_len": 4096, "blocks_per_sm": 1},
+                                    {"warp_max_len": 1 << 20, "schedule": 1, "task_order": 1},
+                                    {"warp_max_len": 1 << 20, "schedule": 1, "task_order": 2},
+                                    {"warp_max_len": 1 << 20, "schedule": 2},
+                                    {"warp_max_len": 64, "chunk_len": 1024, "schedule": 2}])
 def test_schedules_agree(L, tuning):
     b = synth.ragged_batch(num_series=300, lmin=1, lmax=30000, seed=32)
     _, _, res, plan = _run(L, b, "comp", tuning=tuning)
@@ -152,6 +156,25 @@ def test_edge_series(L):
         assert st[0] == "n_too_small" and st[3] == "n_too_small" and st[8] == "n_too_small"
         assert st[9] == "singular" and st[10] == "nonfinite" and st[11] == "bad_interval"
         assert check_batch(L, b, res, "comp") >= 5
+
+
+@pytest.mark.parametrize("tuning", [None, {"warp_max_len": 1 << 20, "schedule": 1},
+                                    {"warp_max_len": 1 << 20, "schedule": 2},
+                                    {"warp_max_len": 256, "chunk_len": 1024}])
+def test_invalid_degrees(L, tuning):
+    """Degrees outside 1..m_max leave a NaN row and the invalid-argument status;
+    the other series of the batch are fitted as usual."""
+    b = synth.ragged_batch(num_series=200, lmin=16, lmax=5000, seed=39)
+    bad = {3: 0, 17: -2, 40: 6, 41: 9, 100: 1000}
+    for s, m in bad.items():
+        b["degree"][s] = m
+    _, _, res, _ = _run(L, b, "comp", tuning=tuning)
+    st = res["status"].cpu().numpy()
+    X = res["X"].cpu().numpy()
+    for s in bad:
+        assert L.STATUS_NAMES[int(st[s])] == "invalid_arg" and np.all(np.isnan(X[s])), s
+    good = [s for s in range(200) if s not in bad]
+    assert check_batch(L, b, res, "comp", series=good) > 180
 
 
 def test_high_degrees(L):

@@ -264,3 +264,28 @@ def test_fused_fit_statuses(L):
     assert L.status_names(out["status"]) == ["ok", "ok", "n_too_small", "n_too_small"]
     out = L.fit_degrees(_dev(np.linspace(-1, 1, 30), f32), _dev(np.ones(30), f32), 2, 1, interval=(3.0, 1.0))
     assert L.status_names(out["status"]) == ["bad_interval", "bad_interval"]
+
+
+# --- alternative solver: Cholesky ---------------------------------------------------------
+
+@pytest.mark.parametrize("m", [1, 3, 5, 8])
+def test_cholesky_solver(L, m):
+    d = synth.precision(n=1 << 18, m=min(m, 5))
+    lo, hi = d["interval"]
+    sums, mp, _ = L.powersums(_dev(d["x"]), _dev(d["y"]), m, "comp", (lo, hi))
+    Xg, Xtg, stg = L.solve(sums, m, m, mp, "comp")
+    Xc, Xtc, stc = L.solve(sums, m, m, mp, "comp", method="cholesky")
+    assert L.status_names(stc) == ["ok"] and L.status_names(stg) == ["ok"]
+    S = sums.cpu().numpy()
+    st, Xo = oracle.solve_cholesky(S[: 2 * m + 1], S[2 * m + 1:], m, eps=oracle.EPS32)
+    assert st == "ok"
+    cond = np.linalg.cond(_hankel(S[: 2 * m + 1], m))
+    assert _rel(Xtc.cpu().numpy(), Xo) <= 1e2 * cond * 2.0 ** -52
+    assert _rel(Xtc.cpu().numpy(), Xtg.cpu().numpy()) <= 1e2 * cond * 2.0 ** -52
+
+
+def test_cholesky_statuses(L):
+    f32 = torch.float32
+    sums, mp, _ = L.powersums(_dev(np.full(50, 2.0), f32), _dev(np.arange(50.0), f32), 2, "comp")
+    X, Xt, st = L.solve(sums, 2, 2, mp, "comp", method="cholesky")
+    assert L.status_names(st) == ["singular"] and torch.isnan(X).all()

@@ -44,6 +44,12 @@ MUTANTS = {
     # adjoint: transpose of the un-map replaced by the un-map itself
     "adjoint_transpose": ("if (map) orc_unmap_transpose(m, map[0], map[1], gX, gt);",
                           "if (map) orc_unmap(m, map[0], map[1], gX, gt);"),
+    # Cholesky: diagonal update sign
+    "cholesky_sign": ("for (int k = 0; k < j; ++k) d -= Lm[j * N + k] * Lm[j * N + k];",
+                      "for (int k = 0; k < j; ++k) d += Lm[j * N + k] * Lm[j * N + k];"),
+    # Cholesky: transposed factor in the back substitution
+    "cholesky_transposed": ("for (int k = i + 1; k < N; ++k) acc -= Lm[k * N + i] * X[k];",
+                            "for (int k = i + 1; k < N; ++k) acc -= Lm[i * N + k] * X[k];"),
     # residual evaluation drops the constant term
     "eval_drop_a0": ("acc += X[j] * p;\n            p *= x[i];\n        }\n        f[i] = acc;",
                      "if (j) acc += X[j] * p;\n            p *= x[i];\n        }\n        f[i] = acc;"),

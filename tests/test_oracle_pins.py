@@ -408,3 +408,33 @@ def test_backward_torch_autograd():
     np.testing.assert_allclose(X.detach().numpy(), out["X"], rtol=1e-9, atol=1e-12)
     np.testing.assert_allclose(dy, yt.grad.numpy(), rtol=1e-7, atol=1e-9 * np.max(np.abs(dy)))
     np.testing.assert_allclose(dx, xt.grad.numpy(), rtol=1e-7, atol=1e-9 * np.max(np.abs(dx)))
+
+
+# --- the alternative solver: Cholesky of the SPD Hankel matrix (Section V) -----------------
+
+@pytest.mark.parametrize("m", [1, 2, 3, 5, 8])
+def test_cholesky_against_lapack_and_gauss(m):
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    d = synth.small_series(3000, seed=1400 + m, m=m, noise=0.05, dtype=np.float64)
+    S, T = oracle.powersums(d["x"], d["y"], m)
+    st, X = oracle.solve_cholesky(S, T, m)
+    assert st == "ok"
+    A = _hankel(S, m)
+    ref = scipy_linalg.cho_solve(scipy_linalg.cho_factor(A, lower=True), T)
+    cond = np.linalg.cond(A)
+    assert np.linalg.norm(X - ref) / np.linalg.norm(ref) <= 1e2 * cond * EPS
+    st2, Xg = oracle.solve(S, T, m)
+    assert np.linalg.norm(X - Xg) / np.linalg.norm(Xg) <= 1e2 * cond * EPS
+
+
+def test_cholesky_table1_and_statuses():
+    _, _, x, y = _table1()
+    for m in (1, 2, 3):
+        S, T = oracle.powersums(x, y, m)
+        st, X = oracle.solve_cholesky(S, T, m)
+        assert st == "ok"
+        np.testing.assert_allclose(X, oracle.fit(x, y, m)["X"], rtol=1e-6)
+    S, T = oracle.powersums(np.full(10, 2.0), np.arange(10.0), 1)
+    assert oracle.solve_cholesky(S, T, 1)[0] == "singular"
+    S, T = oracle.powersums(np.array([1.0, 2.0, 3.0]), np.array([1.0, np.nan, 3.0]), 1)
+    assert oracle.solve_cholesky(S, T, 1)[0] == "nonfinite"

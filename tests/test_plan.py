@@ -39,7 +39,8 @@ def test_cover_and_order(B):
     lens = np.concatenate([[0, 1, 70000, 3], rng.integers(0, 20000, 500)])
     off = np.concatenate([[0], np.cumsum(lens)])
     deg = rng.integers(1, 6, lens.size)
-    rc, plan, bt, wt = build(B, off, deg, warp_max_len=4096, chunk_len=8192)
+    rc, plan, bt, wt = build(B, off, deg, warp_max_len=4096, chunk_len=8192, task_order=2,
+                             schedule=1)
     assert rc == B.OK
     seen = np.zeros(lens.size, dtype=int)
     # block tasks: consecutive chunks of one series, chunk count right, first-task index right
@@ -89,3 +90,32 @@ def test_workspace_sizes(B):
     assert ws % 256 == 0 and ws >= 256 + 16 * 3
     assert B.lib.lsefit_backward_workspace_size(ctypes.byref(plan)) > 0
     assert B.lib.lsefit_range_workspace_size(ctypes.byref(plan)) >= 256 + 16 * 3
+
+
+def test_degree_classes(B):
+    """Default schedule: warp tasks by degree class (degrees outside 1..8 first),
+    longest first within a class; class_begin and class_points describe them."""
+    rng = np.random.default_rng(2)
+    lens = rng.integers(0, 70000, 800)
+    off = np.concatenate([[0], np.cumsum(lens)])
+    deg = rng.integers(1, 6, lens.size)
+    deg[:7] = [0, -3, 9, 100, 8, 7, 6]
+    rc, plan, bt, wt = build(B, off, deg, warp_max_len=1 << 20)
+    assert rc == B.OK and plan.tuning.schedule == 3 and plan.n_block_tasks == 0
+    cls = np.where((deg >= 1) & (deg <= 8), deg, 0)
+    keys = [(cls[s], -lens[s]) for s in wt[:, 0]]
+    assert keys == sorted(keys)
+    begin = list(plan.class_begin)
+    assert begin[0] == 0 and begin[-1] == plan.n_warp_tasks and begin == sorted(begin)
+    for c in range(9):
+        members = wt[begin[c]:begin[c + 1], 0]
+        assert np.all(cls[members] == c) and members.size == np.count_nonzero(cls == c)
+        assert plan.class_points[c] == lens[cls == c].sum()
+
+
+def test_degree_classes_without_degrees(B):
+    lens = np.array([5, 100, 7, 100, 3000])
+    off = np.concatenate([[0], np.cumsum(lens)])
+    rc, plan, bt, wt = build(B, off, warp_max_len=1 << 20)
+    assert rc == B.OK
+    assert list(plan.class_begin) == [0] + [5] * 9 and plan.class_points[0] == lens.sum()
