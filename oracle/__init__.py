@@ -11,7 +11,9 @@ T_k = sum x^k y (k <= m), the Hankel normal matrix A[j][k] = S_{j+k},
 B[j] = T_j, and Gaussian elimination of AX = B.  Two independent validators
 sit beside it: ``exact`` (the same definition in exact rational arithmetic)
 and ``householder`` (the Vandermonde QR least-squares solve that Section III
-describes for MATLAB's polyfit).
+describes for MATLAB's polyfit).  ``fit_general`` generalises the objective
+to per-point weights and to the Chebyshev basis, from the definition of its
+normal equations.
 
 Readings where the paper is silent or misprinted are listed at the top of
 ``lsefit_oracle.c``.  Parity unpinned: the correlation coefficient "R" of
@@ -85,6 +87,11 @@ def _load():
         lib.orc_sse.restype = ctypes.c_double
         lib.orc_backward.argtypes = [dp, dp, i64, ctypes.c_int, dp, dp, dp, dp, ctypes.c_double, dp, dp]
         lib.orc_backward.restype = ctypes.c_int
+        lib.orc_fit_general.argtypes = [dp, dp, dp, i64, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double,
+                                        dp, dp, dp, dp]
+        lib.orc_fit_general.restype = ctypes.c_int
+        lib.orc_cheb_to_mono.argtypes = [ctypes.c_int, dp, dp]
+        lib.orc_cheb_to_mono.restype = None
         lib.orc_max_degree.argtypes = []
         lib.orc_max_degree.restype = ctypes.c_int
         _lib = lib
@@ -220,3 +227,50 @@ def backward(x, y, m: int, cs, S, Xt, gX, eps: float = EPS64):
     st = _load().orc_backward(_ptr(x), _ptr(y), x.size, m, _ptr(mp) if mp is not None else None,
                               _ptr(S), _ptr(Xt), _ptr(gX), float(eps), _ptr(dx), _ptr(dy))
     return STATUS_NAMES[st], dx, dy
+
+
+BASES = {"monomial": 0, "chebyshev": 1}
+
+
+def cheb_to_mono(a):
+    """Monomial coefficients of sum_k a[k] T_k(t)."""
+    a = _f64(a)
+    out = np.zeros_like(a)
+    _load().orc_cheb_to_mono(a.size - 1, _ptr(a), _ptr(out))
+    return out
+
+
+def fit_general(x, y, m: int, w=None, basis: str = "monomial", cs=None, eps: float = EPS64) -> dict:
+    """Weighted and/or Chebyshev-basis fit: minimises sum_i w_i (y_i - f(t_i))^2
+    with f = sum_k Xb[k] phi_k(t), phi_k = t^k or T_k(t); t = s(x - c) when
+    cs = (c, s).  Returns dict(status, X (x monomials), Xb, G, b)."""
+    x = _f64(x)
+    y = _f64(y)
+    assert x.shape == y.shape and x.ndim == 1
+    wa = _f64(w) if w is not None else None
+    if wa is not None:
+        assert wa.shape == x.shape
+    n1 = m + 1
+    X = np.zeros(n1)
+    Xb = np.zeros(n1)
+    G = np.zeros(n1 * n1)
+    b = np.zeros(n1)
+    mp = _f64(cs) if cs is not None else None
+    st = _load().orc_fit_general(_ptr(x), _ptr(y), _ptr(wa) if wa is not None else None, x.size, m,
+                                 BASES[basis], _ptr(mp) if mp is not None else None, float(eps),
+                                 _ptr(X), _ptr(Xb), _ptr(G), _ptr(b))
+    return {"status": STATUS_NAMES[st], "X": X, "Xb": Xb, "G": G.reshape(n1, n1), "b": b}
+
+
+def fit_general_interval(x, y, m: int, lo: float, hi: float, fp32: bool, w=None,
+                         basis: str = "monomial") -> dict:
+    """fit_general on the map of [lo, hi] onto [-1, 1] (constants and threshold as fit_interval)."""
+    st, c, s = map_constants(lo, hi, fp32)
+    if st != "ok":
+        n1 = m + 1
+        return {"status": st, "X": np.full(n1, np.nan), "Xb": np.full(n1, np.nan), "G": None, "b": None,
+                "c": np.nan, "s": np.nan}
+    out = fit_general(x, y, m, w=w, basis=basis, cs=(c, s), eps=EPS32 if fp32 else EPS64)
+    out["c"] = c
+    out["s"] = s
+    return out

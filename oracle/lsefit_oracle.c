@@ -36,7 +36,10 @@
  *     (s(x - c))^k;
  *   - the adjoint of the fit (derived by the chain rule from the normal
  *     equations): with lambda solving A lambda = dL/dXt,
- *     dL/dy_i = lambda(t_i) and dL/dt_i = lambda'(t_i) r_i - lambda(t_i) f'(t_i).
+ *     dL/dy_i = lambda(t_i) and dL/dt_i = lambda'(t_i) r_i - lambda(t_i) f'(t_i);
+ *   - two generalisations of the objective (Section V leaves higher-order
+ *     fits and other solution methods open): per-point weights w_i, and the
+ *     Chebyshev basis T_k(t) in place of t^k (orc_fit_general).
  *
  * Build: cc -O2 -ffp-contract=off -fPIC -shared lsefit_oracle.c -lm
  * (-ffp-contract=off keeps every product and sum a separately rounded IEEE
@@ -342,5 +345,90 @@ int orc_backward(const double* x, const double* y, int64_t n, int m, const doubl
         dy[i] = lv;
         dx[i] = sc * (ld * (y[i] - fv) - lv * fd);
     }
+    return ORC_OK;
+}
+
+/*
+ * Generalised objective: Pi_w = sum_i w_i [y_i - f(t_i)]^2 with
+ * f(t) = sum_k a_k phi_k(t), where phi_k(t) = t^k (basis 0) or the
+ * Chebyshev polynomial T_k(t) (basis 1: T_0 = 1, T_1 = t,
+ * T_{k+1} = 2 t T_k - T_{k-1}).  w == NULL means w_i = 1.
+ * Setting dPi_w/da_j = 0 as in Section II gives the normal equations
+ * G a = b with G[j][k] = sum_i w_i phi_j(t_i) phi_k(t_i) and
+ * b[j] = sum_i w_i phi_j(t_i) y_i.  Written out from that definition: for
+ * every point the basis values, then the double loop over (j, k).  Solved by
+ * the same Gaussian elimination and singularity threshold as orc_solve, with
+ * max|G| over the entries of G.
+ * Outputs: Xb (coefficients a_k in the chosen basis of t), X (monomial
+ * coefficients of x: the basis expanded into powers of t, then un-mapped),
+ * and optionally G ((m+1)^2, row-major) and b (m+1).  n < m+1 points is
+ * N_TOO_SMALL whatever the weights (zero weights show up as SINGULAR).
+ */
+static void orc_basis(int m, int basis, double t, double* phi)
+{
+    phi[0] = 1.0;
+    if (m >= 1) phi[1] = t;
+    for (int k = 2; k <= m; ++k)
+        phi[k] = basis == 1 ? 2.0 * t * phi[k - 1] - phi[k - 2] : phi[k - 1] * t;
+}
+
+/* Monomial coefficients of sum_k a[k] T_k(t): P[k][j] = coefficient of t^j
+ * in T_k, from the same recurrence applied to coefficient rows. */
+void orc_cheb_to_mono(int m, const double* a, double* out)
+{
+    double P[(ORC_MAX_M + 1) * (ORC_MAX_M + 1)];
+    const int N = m + 1;
+    for (int i = 0; i < N * N; ++i) P[i] = 0.0;
+    P[0] = 1.0;
+    if (m >= 1) P[1 * N + 1] = 1.0;
+    for (int k = 2; k <= m; ++k)
+        for (int j = 0; j <= k; ++j)
+            P[k * N + j] = (j > 0 ? 2.0 * P[(k - 1) * N + j - 1] : 0.0) - P[(k - 2) * N + j];
+    for (int j = 0; j < N; ++j) {
+        double acc = 0.0;
+        for (int k = j; k < N; ++k) acc += a[k] * P[k * N + j];
+        out[j] = acc;
+    }
+}
+
+int orc_fit_general(const double* x, const double* y, const double* w, int64_t n, int m, int basis,
+                    const double* map, double eps, double* X, double* Xb, double* G_out, double* b_out)
+{
+    if (m < 1 || m > ORC_MAX_M || (basis != 0 && basis != 1)) return ORC_BAD_ARG;
+    const int N = m + 1;
+    double G[(ORC_MAX_M + 1) * (ORC_MAX_M + 1)], b[ORC_MAX_M + 1], phi[ORC_MAX_M + 1], a[ORC_MAX_M + 1];
+    for (int i = 0; i < N * N; ++i) G[i] = 0.0;
+    for (int j = 0; j < N; ++j) b[j] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double t = map ? map[1] * (x[i] - map[0]) : x[i];
+        const double wi = w ? w[i] : 1.0;
+        orc_basis(m, basis, t, phi);
+        for (int j = 0; j < N; ++j) {
+            for (int k = 0; k < N; ++k) G[j * N + k] += wi * phi[j] * phi[k];
+            b[j] += wi * phi[j] * y[i];
+        }
+    }
+    if (G_out) memcpy(G_out, G, sizeof(double) * N * N);
+    if (b_out) memcpy(b_out, b, sizeof(double) * N);
+    int st = ORC_OK;
+    if (n < m + 1) st = ORC_N_TOO_SMALL;
+    for (int i = 0; st == ORC_OK && i < N * N; ++i)
+        if (!isfinite(G[i])) st = ORC_NONFINITE;
+    for (int j = 0; st == ORC_OK && j < N; ++j)
+        if (!isfinite(b[j])) st = ORC_NONFINITE;
+    if (st == ORC_OK) st = orc_gauss_inplace(m, G, b, a, eps);
+    if (st != ORC_OK) {
+        for (int j = 0; j < N; ++j) {
+            X[j] = NAN;
+            if (Xb) Xb[j] = NAN;
+        }
+        return st;
+    }
+    double Xt[ORC_MAX_M + 1];
+    if (basis == 1) orc_cheb_to_mono(m, a, Xt);
+    else memcpy(Xt, a, sizeof(double) * N);
+    if (Xb) memcpy(Xb, a, sizeof(double) * N);
+    if (map) orc_unmap(m, map[0], map[1], Xt, X);
+    else memcpy(X, Xt, sizeof(double) * N);
     return ORC_OK;
 }

@@ -50,6 +50,14 @@ MUTANTS = {
     # Cholesky: transposed factor in the back substitution
     "cholesky_transposed": ("for (int k = i + 1; k < N; ++k) acc -= Lm[k * N + i] * X[k];",
                             "for (int k = i + 1; k < N; ++k) acc -= Lm[i * N + k] * X[k];"),
+    # Chebyshev recurrence with the wrong sign
+    "cheb_recurrence_sign": ("2.0 * t * phi[k - 1] - phi[k - 2]", "2.0 * t * phi[k - 1] + phi[k - 2]"),
+    # weight applied twice in the normal matrix
+    "weight_squared": ("G[j * N + k] += wi * phi[j] * phi[k];", "G[j * N + k] += wi * wi * phi[j] * phi[k];"),
+    # weight dropped from the right-hand side
+    "weight_dropped_rhs": ("b[j] += wi * phi[j] * y[i];", "b[j] += phi[j] * y[i];"),
+    # Chebyshev-to-monomial expansion without the shift by one power
+    "cheb_to_mono_shift": ("(j > 0 ? 2.0 * P[(k - 1) * N + j - 1] : 0.0)", "(j > 0 ? 2.0 * P[(k - 1) * N + j] : 0.0)"),
     # residual evaluation drops the constant term
     "eval_drop_a0": ("acc += X[j] * p;\n            p *= x[i];\n        }\n        f[i] = acc;",
                      "if (j) acc += X[j] * p;\n            p *= x[i];\n        }\n        f[i] = acc;"),

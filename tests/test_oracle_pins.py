@@ -438,3 +438,104 @@ def test_cholesky_table1_and_statuses():
     assert oracle.solve_cholesky(S, T, 1)[0] == "singular"
     S, T = oracle.powersums(np.array([1.0, 2.0, 3.0]), np.array([1.0, np.nan, 3.0]), 1)
     assert oracle.solve_cholesky(S, T, 1)[0] == "nonfinite"
+
+
+# --- Generalised objective: per-point weights and the Chebyshev basis ----------------
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("m", [1, 3, 5])
+def test_weighted_against_lstsq(m):
+    """Weighted LSE = ordinary least squares of the sqrt(w)-scaled Vandermonde system."""
+    rng = np.random.default_rng(1500 + m)
+    x = rng.uniform(-1.0, 1.0, 800)
+    y = np.polynomial.polynomial.polyval(x, rng.normal(size=m + 1)) + rng.normal(0, 0.05, x.size)
+    w = rng.uniform(0.05, 3.0, x.size)
+    r = oracle.fit_general(x, y, m, w=w)
+    assert r["status"] == "ok"
+    V = np.vander(x, m + 1, increasing=True) * np.sqrt(w)[:, None]
+    ref = np.linalg.lstsq(V, y * np.sqrt(w), rcond=None)[0]
+    cond = np.linalg.cond(r["G"])
+    assert _rel(r["X"], ref) <= 1e2 * cond * EPS
+    # the weights matter: the unweighted fit differs
+    assert _rel(oracle.fit(x, y, m)["X"], ref) > 1e3 * cond * EPS
+
+
+@pytest.mark.parametrize("basis", ["monomial", "chebyshev"])
+def test_integer_weights_are_repeated_points(basis):
+    """An integer weight w_i is the point (x_i, y_i) taken w_i times (brute force)."""
+    rng = np.random.default_rng(1510)
+    x = rng.uniform(-2.0, 3.0, 60)
+    y = rng.normal(size=x.size)
+    w = rng.integers(0, 5, x.size).astype(np.float64)
+    m = 3
+    cs = (0.5, 0.4)
+    r = oracle.fit_general(x, y, m, w=w, basis=basis, cs=cs)
+    xr, yr = np.repeat(x, w.astype(int)), np.repeat(y, w.astype(int))
+    ref = oracle.fit_interval(xr, yr, m, -2.0, 3.0, fp32=False)
+    assert r["status"] == "ok" and ref["status"] == "ok"
+    cond = np.linalg.cond(r["G"])
+    assert _rel(r["X"], ref["X"]) <= 1e3 * cond * EPS
+
+
+@pytest.mark.parametrize("m", [2, 4, 8])
+def test_chebyshev_against_chebfit(m):
+    """Chebyshev coefficients of the (weighted) fit equal numpy's chebfit, an
+    independent least-squares solve of the Chebyshev-Vandermonde system."""
+    rng = np.random.default_rng(1520 + m)
+    t = rng.uniform(-1.0, 1.0, 1500)
+    y = np.cos(3 * t) + rng.normal(0, 0.01, t.size)
+    w = rng.uniform(0.2, 2.0, t.size)
+    for ww in (None, w):
+        r = oracle.fit_general(t, y, m, w=ww, basis="chebyshev")
+        assert r["status"] == "ok"
+        ref = np.polynomial.chebyshev.chebfit(t, y, m, w=None if ww is None else np.sqrt(ww))
+        assert _rel(r["Xb"], ref) <= 1e3 * np.linalg.cond(r["G"]) * EPS
+
+
+def test_chebyshev_nodes_closed_form():
+    """At the n Chebyshev nodes t_i = cos(pi (i + 1/2) / n) the basis is
+    discretely orthogonal: G = diag(n, n/2, ..., n/2) and a_k = (2/n) sum_i
+    y_i cos(k theta_i) (a_0 with 1/n)."""
+    n, m = 64, 7
+    theta = np.pi * (np.arange(n) + 0.5) / n
+    t = np.cos(theta)
+    y = np.exp(t) * np.sin(2 * t)
+    r = oracle.fit_general(t, y, m, basis="chebyshev")
+    assert r["status"] == "ok"
+    np.testing.assert_allclose(r["G"], np.diag([n] + [n / 2] * m), atol=1e-12 * n)
+    a = np.array([(1.0 if k == 0 else 2.0) / n * np.sum(y * np.cos(k * theta)) for k in range(m + 1)])
+    np.testing.assert_allclose(r["Xb"], a, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("m", [1, 3, 6, 9])
+def test_cheb_to_mono_against_numpy(m):
+    a = np.random.default_rng(1530 + m).normal(size=m + 1)
+    np.testing.assert_allclose(oracle.cheb_to_mono(a), np.polynomial.chebyshev.cheb2poly(a),
+                               rtol=1e-13, atol=1e-13 * 2.0 ** m)
+
+
+def test_chebyshev_and_monomial_fit_the_same_polynomial():
+    """Both bases span the polynomials of degree <= m, so the minimiser is the
+    same function: equal x-basis coefficients (Table I, mapped and not)."""
+    _, _, x, y = _table1()
+    for m in (1, 2, 3):
+        ref = oracle.fit(x, y, m)["X"]
+        for cs in (None, (np.mean(x), 2.0 / (x.max() - x.min()))):
+            r = oracle.fit_general(x, y, m, basis="chebyshev", cs=cs)
+            assert r["status"] == "ok"
+            assert _rel(r["X"], ref) <= 1e-8
+        rw = oracle.fit_general(x, y, m, w=np.ones_like(x))
+        assert _rel(rw["X"], ref) <= 1e-8
+
+
+def test_general_statuses():
+    x = np.array([0.0, 1.0, 2.0])
+    assert oracle.fit_general(x, x, 3, basis="chebyshev")["status"] == "n_too_small"
+    assert oracle.fit_general(x, x, 2, w=np.array([1.0, 0.0, 1.0]))["status"] == "singular"
+    assert oracle.fit_general(x, np.array([0.0, np.nan, 1.0]), 1, basis="chebyshev")["status"] == "nonfinite"
+    assert oracle.fit_general(x, x, 1, w=np.array([1.0, np.inf, 1.0]))["status"] == "nonfinite"
+    assert oracle.fit_general(np.full(5, 0.3), np.arange(5.0), 1, basis="chebyshev")["status"] == "singular"
+    assert oracle.fit_general_interval(x, x, 1, 1.0, 1.0, fp32=False)["status"] == "bad_interval"
