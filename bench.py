@@ -47,7 +47,9 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["lsefit", "reference"], default="lsefit")
     p.add_argument("--workload", default="single_large",
-                   choices=["single_large", "ragged_batch", "diff_batch", "single_fp64"])
+                   choices=["single_large", "ragged_batch", "diff_batch", "single_fp64", "general"])
+    p.add_argument("--kind", default="weighted", choices=["weighted", "chebyshev", "weighted_chebyshev"],
+                   help="objective of the general workload")
     p.add_argument("--n", type=int, default=1 << 28, help="points of the single_large series")
     p.add_argument("--series", type=int, default=65536, help="series of the ragged_batch workload")
     p.add_argument("--no-plain", action="store_true", help="skip the plain per-series comparison")
@@ -701,6 +703,129 @@ def run_single_fp64(args, dist: Dist):
             "gpu_launches": args.steps}
 
 
+# ---------------------------------------------------------------------------
+# general: the weighted and Chebyshev-basis fits of one long series
+# ---------------------------------------------------------------------------
+GENERAL_KINDS = {
+    # kind: (weights, basis, degree, interval, description)
+    "weighted": (True, "monomial", 3, (-1.0, 1.0),
+                 "single series, n=2^28 FP32 points + FP32 weights (3 GiB), x ~ U[-1,1], w ~ U[0.1,3], "
+                 "weighted degrees 3,2,1 from one pass"),
+    "chebyshev": (False, "chebyshev", 8, (0.0, 1000.0),
+                  "single series, n=2^28 FP32 points (2 GiB), x ~ U[0,1000] mapped to [-1,1], "
+                  "Chebyshev basis, degrees 8..1 from one pass"),
+    "weighted_chebyshev": (True, "chebyshev", 8, (0.0, 1000.0),
+                           "single series, n=2^28 FP32 points + FP32 weights (3 GiB), x ~ U[0,1000] mapped, "
+                           "weighted Chebyshev basis, degrees 8..1 from one pass"),
+}
+
+
+def cpu_baseline_general(x, y, w, m, basis, interval, target_s):
+    import oracle
+    n = x.size
+    sample = min(n, 1 << 22)
+    xs = x[:sample].astype(np.float64)
+    ys = y[:sample].astype(np.float64)
+    ws = w[:sample].astype(np.float64) if w is not None else None
+    reps, t_total = 0, 0.0
+    while reps < 3 or t_total < target_s:
+        t0 = time.perf_counter()
+        out = oracle.fit_general_interval(xs, ys, m, *interval, fp32=True, w=ws, basis=basis)
+        t_total += time.perf_counter() - t0
+        reps += 1
+        if reps >= 1000:
+            break
+    assert out["status"] == "ok"
+    return {"value": sample * reps / t_total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {sample} points of the series, degree {m} {basis} fit"
+                      f"{' with weights' if w is not None else ''} (FP64 normal equations from their "
+                      f"definition, sequential C), {reps} repetitions, {t_total:.1f} s"}
+
+
+def run_general(args, dist: Dist):
+    import torch
+    import synth
+    import paper_1512_08017_gb300 as L
+
+    weighted, basis, m, interval, desc = GENERAL_KINDS[args.kind]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = args.n
+    hx = torch.empty(n, dtype=torch.float32).pin_memory()
+    hy = torch.empty(n, dtype=torch.float32).pin_memory()
+    hw = torch.empty(n, dtype=torch.float32).pin_memory() if weighted else None
+    d = synth.single_large(n=n, m=m, seed=synth.SEED_SINGLE_LARGE + dist.rank, out_x=hx.numpy(),
+                           out_y=hy.numpy())
+    lo, hi = interval
+    if (lo, hi) != (-1.0, 1.0):  # the same polynomial of t, on x = lo + (t + 1) (hi - lo) / 2
+        xn = hx.numpy()
+        np.multiply(xn + np.float32(1.0), np.float32((hi - lo) / 2), out=xn)
+        xn += np.float32(lo)
+    if weighted:
+        synth.weights(n, seed=synth.SEED_WEIGHTS + dist.rank, out=hw.numpy())
+    x, y = hx.to(dev), hy.to(dev)
+    w = hw.to(dev) if weighted else None
+    stream = torch.cuda.current_stream()
+    out = L.fit_general(x, y, m, w=w, basis=basis, m_lo=1, accum=args.accum, interval=interval)
+
+    def step():
+        L.fit_general(x, y, m, w=w, basis=basis, m_lo=1, accum=args.accum, interval=interval, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert out["status"].tolist() == [L.OK] * m
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    per, total = _event_steps(step, args.steps, stream)
+    dist.barrier()
+    clk = clocks.stop()
+    ms_max = dist.max(total)
+    kern_ms = dist.max(statistics.mean(per))
+    streams = 3 if weighted else 2
+    algo_bytes = 4 * streams * n
+
+    e2e = None
+    if not args.no_e2e:
+        hX = torch.empty(m + 1, dtype=torch.float64).pin_memory()
+        e_steps = max(3, min(args.steps, 10))
+
+        def e2e_step():
+            x.copy_(hx, non_blocking=True)
+            y.copy_(hy, non_blocking=True)
+            if weighted:
+                w.copy_(hw, non_blocking=True)
+            step()
+            hX.copy_(out["X"][m - 1], non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        dist.barrier()
+        _, e_total = _event_steps(e2e_step, e_steps, stream)
+        e_ms = dist.max(e_total)
+        e2e = {"value": dist.world * n * e_steps / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": streams * n * 4, "d2h_bytes_per_step": (m + 1) * 8,
+               "steps": e_steps, "ms_per_step": e_ms / e_steps}
+    kname = "gen_kernel_f32<{},F32,{},W={},CHEB={}>".format(m, args.accum, int(weighted), int(basis == "chebyshev"))
+    cpu = None
+    if dist.rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_general(d["x"] if (lo, hi) == (-1.0, 1.0) else hx.numpy(), d["y"],
+                                   hw.numpy() if weighted else None, m, basis, interval, args.cpu_seconds)
+    return {
+        "metric": METRIC, "value": dist.world * n * args.steps / (ms_max / 1e3), "unit": UNIT,
+        "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded)",
+        "config": {"workload": desc, "n": n, "m": list(range(m, 0, -1)), "basis": basis, "weighted": weighted,
+                   "accum": args.accum, "l2": "inputs larger than L2; no flush",
+                   "parallelism": f"replicas x{dist.world}"},
+        "roofline": _roofline(algo_bytes, kern_ms, kname, f"general_{args.kind}"),
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": args.steps,
+    }
+
+
 def run_reference(args, dist: Dist):
     """The oracle timed on the host cores on the same workload and metric."""
     if dist.rank != 0:
@@ -750,7 +875,7 @@ def main(argv=None):
     dist = Dist(args.gpus)
     try:
         runners = {"single_large": run_single_large, "ragged_batch": run_ragged_batch,
-                   "diff_batch": run_diff_batch, "single_fp64": run_single_fp64}
+                   "diff_batch": run_diff_batch, "single_fp64": run_single_fp64, "general": run_general}
         line = runners[args.workload](args, dist)
         if dist.rank == 0 and line is not None:
             print(json.dumps(line))

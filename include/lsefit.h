@@ -217,6 +217,61 @@ int lsefit_fit_noalloc(const void* x, const void* y, int64_t n, int dtype, int m
                        int32_t* status, lsefit_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Generalised objective: per-point weights, Chebyshev basis
+ * ------------------------------------------------------------------------ */
+
+/* Basis of the fitted polynomial in the mapped variable t. */
+enum {
+    LSEFIT_BASIS_MONOMIAL = 0,  /* phi_k(t) = t^k (the paper's basis) */
+    LSEFIT_BASIS_CHEBYSHEV = 1  /* phi_k(t) = T_k(t): T_0 = 1, T_1 = t, T_{k+1} = 2 t T_k - T_{k-1} */
+};
+
+/* Bytes of workspace lsefit_fit_general needs (any n, any device). */
+size_t lsefit_fit_general_workspace_size(int m);
+
+/*
+ * lsefit_fit_general -- the fit of Section II for the objective
+ * sum_i w_i [y_i - f(t_i)]^2 with f(t) = sum_k a_k phi_k(t) (Section V
+ * leaves higher-order fits open; weights and the Chebyshev basis are this
+ * library's generalisations).  Setting the derivatives by a_j to zero gives
+ * G a = b with G[j][k] = sum w phi_j phi_k and b[j] = sum w phi_j y.  One
+ * streaming pass accumulates the moments M_p = sum w phi_p(t) (p <= 2m) and
+ * T_j = sum w phi_j(t) y (j <= m); G is M_{j+k} (monomial) or
+ * (M_{j+k} + M_{|j-k|}) / 2 (Chebyshev: T_j T_k = (T_{j+k} + T_{|j-k|}) / 2).
+ * G a = b is solved by Gaussian elimination with partial pivoting in FP64
+ * (singular when a pivot is at or below (m+1) * eps * max|G|, eps as in
+ * lsefit_solve).
+ *
+ *  x, y, w    device (or mapped host) arrays of n points of `dtype`; w may be
+ *             NULL (every w_i = 1).  Weights are the caller's: zero weights
+ *             drop points (and may leave G singular), negative weights give
+ *             the stationary point of the objective, not a minimum.
+ *  n, dtype, m, m_lo, accum, interval
+ *             as lsefit_fit (degrees m_lo..m from the one pass; the map
+ *             t = s (x - c) of [lo, hi] onto [-1, 1] or t = x without an
+ *             interval).  dtype F64 requires accum F64.
+ *  basis      LSEFIT_BASIS_MONOMIAL or LSEFIT_BASIS_CHEBYSHEV.
+ *  X          device double[(m - m_lo + 1)][m + 1]: monomial coefficients of x
+ *             (row d - m_lo for degree d, entries beyond d zero; NaN rows for
+ *             failed fits).
+ *  Xb         device double[(m - m_lo + 1)][m + 1] or NULL: coefficients a_k in
+ *             the basis of t (Chebyshev coefficients with BASIS_CHEBYSHEV).
+ *  sums       device double[3m + 2] or NULL: M_0..M_2m then T_0..T_m (without
+ *             weights M_0 = n).
+ *  map        device double[2] or NULL: (c, s) used.
+ *  status     device int32[m - m_lo + 1]: per-degree status.
+ *  workspace  device, >= lsefit_fit_general_workspace_size(m) bytes,
+ *             256-byte aligned, zero-filled once before first use (each call
+ *             leaves it zeroed).  One workspace serves one call at a time.
+ * Returns LSEFIT_OK or a host error; w == NULL with the monomial basis runs
+ * lsefit_fit itself (Xb is then the mapped-basis coefficients Xt).
+ */
+int lsefit_fit_general(const void* x, const void* y, const void* w, int64_t n, int dtype, int m, int m_lo,
+                       int accum, int basis, const double* interval, double* X, double* Xb, double* sums,
+                       double* map, int32_t* status, void* workspace, size_t workspace_bytes,
+                       lsefit_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Batched ragged series (one persistent launch)
  * ------------------------------------------------------------------------ */
 

@@ -38,6 +38,23 @@ int occupancy_blocks(const void* kernel, int threads, size_t smem) {
     return nb;
 }
 
+// Device address of a point array: device/managed memory as is; host memory
+// only when it is registered with CUDA (pinned), through the address CUDA
+// reports for it.  Unregistered host memory is rejected.
+int resolve_device_pointer(const void*& ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return LSEFIT_ERR_INVALID_ARG;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return LSEFIT_OK;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer != nullptr) {
+        ptr = a.devicePointer;
+        return LSEFIT_OK;
+    }
+    return LSEFIT_ERR_INVALID_ARG;
+}
+
 }  // namespace lsefit
 
 extern "C" const char* lsefit_status_string(int code) {

@@ -504,23 +504,13 @@ __host__ __device__ constexpr double singular_eps(int accum) {
 // Gaussian elimination with partial pivoting of the padded system
 // [[A, 0], [0, I]] z = [rhs, 0] with A[j][k] = S[j+k] (j, k <= m).
 // Returns LSEFIT_OK or LSEFIT_ERR_SINGULAR; z[0..m] is the solution.
+// Gaussian elimination with partial pivoting of the padded system A z = r
+// (A[.][N] holds r; rows and columns beyond m are the identity), then back
+// substitution.  A pivot of a row <= m at or below tol is singular.
 template <int NMAX>
-__device__ __forceinline__ int hankel_ge(int m, const double* S, const double* rhs, double* z, double eps) {
+__device__ __forceinline__ int ge_padded(int m, double (&A)[NMAX + 1][NMAX + 2], double tol, double* z) {
     constexpr int N = NMAX + 1;
     int st = LSEFIT_OK;
-    double A[N][N + 1];
-    // max|A| over the 2m+1 distinct entries S_0..S_2m of the Hankel matrix
-    double amax = 0.0;
-#pragma unroll
-    for (int k = 0; k <= 2 * NMAX; ++k)
-        if (k <= 2 * m) amax = fmax(amax, fabs(S[k]));
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-#pragma unroll
-        for (int k = 0; k < N; ++k) A[j][k] = (j <= m && k <= m) ? S[j + k] : ((j == k) ? 1.0 : 0.0);
-        A[j][N] = (j <= m) ? rhs[j] : 0.0;
-    }
-    const double tol = (double)(m + 1) * eps * amax;
     double inv_piv[N];  // reciprocal of each pivot, reused by the back-substitution
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -570,6 +560,24 @@ __device__ __forceinline__ int hankel_ge(int m, const double* S, const double* r
         if (!zf) st = LSEFIT_ERR_SINGULAR;
     }
     return st;
+}
+
+template <int NMAX>
+__device__ __forceinline__ int hankel_ge(int m, const double* S, const double* rhs, double* z, double eps) {
+    constexpr int N = NMAX + 1;
+    double A[N][N + 1];
+    // max|A| over the 2m+1 distinct entries S_0..S_2m of the Hankel matrix
+    double amax = 0.0;
+#pragma unroll
+    for (int k = 0; k <= 2 * NMAX; ++k)
+        if (k <= 2 * m) amax = fmax(amax, fabs(S[k]));
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) A[j][k] = (j <= m && k <= m) ? S[j + k] : ((j == k) ? 1.0 : 0.0);
+        A[j][N] = (j <= m) ? rhs[j] : 0.0;
+    }
+    return ge_padded<NMAX>(m, A, (double)(m + 1) * eps * amax, z);
 }
 
 // Cholesky factorisation of the padded system (the Hankel matrix is
@@ -639,24 +647,11 @@ __device__ __forceinline__ int fit_precheck(int m, const double* S, const double
     return fin ? LSEFIT_OK : LSEFIT_ERR_NONFINITE;
 }
 
-template <int NMAX, bool CHOL = false>
-__device__ int solve_hankel_rt(int m, const double* S, const double* T, double c, double s,
-                               bool map_ok, double eps, double* Xt, double* X, int ncoef) {
+// Un-map of t-basis coefficients z (k <= m) to the monomials of x:
+// out_j = sum_{k>=j} z_k C(k,j) s^k (-c)^(k-j).
+template <int NMAX>
+__device__ __forceinline__ void unmap_padded(int m, const double* z, double c, double s, double* out) {
     constexpr int N = NMAX + 1;
-    double z[N];
-    int st = fit_precheck(m, S, T, map_ok);
-    if (st == LSEFIT_OK) st = CHOL ? hankel_cholesky<NMAX>(m, S, T, z, eps) : hankel_ge<NMAX>(m, S, T, z, eps);
-    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
-    if (st != LSEFIT_OK) {
-        for (int i = 0; i < ncoef; ++i) {
-            const double v = i <= m ? qnan : 0.0;
-            if (Xt) Xt[i] = v;
-            X[i] = v;
-        }
-        return st;
-    }
-    // un-map: X_j = sum_{k>=j} z_k C(k,j) s^k (-c)^(k-j), over k <= m only
-    double out[N];
     double binom[N];  // row k of Pascal's triangle
 #pragma unroll
     for (int j = 0; j < N; ++j) {
@@ -682,6 +677,26 @@ __device__ int solve_hankel_rt(int m, const double* S, const double* T, double c
             }
         }
     }
+}
+
+template <int NMAX, bool CHOL = false>
+__device__ int solve_hankel_rt(int m, const double* S, const double* T, double c, double s,
+                               bool map_ok, double eps, double* Xt, double* X, int ncoef) {
+    constexpr int N = NMAX + 1;
+    double z[N];
+    int st = fit_precheck(m, S, T, map_ok);
+    if (st == LSEFIT_OK) st = CHOL ? hankel_cholesky<NMAX>(m, S, T, z, eps) : hankel_ge<NMAX>(m, S, T, z, eps);
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    if (st != LSEFIT_OK) {
+        for (int i = 0; i < ncoef; ++i) {
+            const double v = i <= m ? qnan : 0.0;
+            if (Xt) Xt[i] = v;
+            X[i] = v;
+        }
+        return st;
+    }
+    double out[N];
+    unmap_padded<NMAX>(m, z, c, s, out);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         if (i < ncoef) {

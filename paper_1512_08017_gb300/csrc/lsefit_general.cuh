@@ -1,0 +1,506 @@
+// lsefit_general.cuh -- the generalised objective: per-point weights and the
+// Chebyshev basis.
+//
+// Section II minimises sum_i [y_i - f(x_i)]^2 over the monomials of x.  Two
+// generalisations keep its single pass and its small dense solve:
+//   * weights: sum_i w_i [y_i - f(t_i)]^2.  The normal matrix and right-hand
+//     side take a factor w_i in every sum: M_k = sum w t^k, T_k = sum w t^k y;
+//   * the Chebyshev basis f(t) = sum_k a_k T_k(t) (T_0 = 1, T_1 = t,
+//     T_{k+1} = 2 t T_k - T_{k-1}), which stays well conditioned on [-1, 1]
+//     where the monomial Hankel matrix does not.  The product identity
+//     T_j T_k = (T_{j+k} + T_{|j-k|}) / 2 makes the normal matrix
+//     G[j][k] = (C_{j+k} + C_{|j-k|}) / 2 a function of the 2m+1 moments
+//     C_p = sum w T_p(t), so the pass still keeps 3m+1 (+1) accumulators.
+// Both run the basis recurrence on w-scaled values: b_0 = w, b_1 = w t, then
+// b_{k+1} = 2 t b_k - b_{k-1} (Chebyshev) or b_{k+1} = t b_k (monomial).
+#pragma once
+
+#include "lsefit_device.cuh"
+
+namespace lsefit {
+
+__device__ __forceinline__ u64 neg2(u64 a) { return a ^ 0x8000000080000000ull; }
+
+// Accumulator slots: 0..2M the moments M_k = sum w phi_k(t), 2M+1..3M+1 the
+// right-hand sides T_k = sum w phi_k(t) y.  Without weights slot 0 (the
+// point count) is not accumulated.  The `w` operand of add_pair is the
+// weight pair, or, without weights, 1 for a point and 0 for an empty lane
+// (it seeds the Chebyshev recurrence, in which an empty lane with t = 0
+// would otherwise give T_2(0) = -1).
+template <int M, bool COMP, bool W, bool CHEB>
+struct AccGenF32 {
+    static constexpr int N = 3 * M + 2;
+    static constexpr int K0 = W ? 0 : 1;
+    u64 acc[N];
+    u64 phi[COMP ? N : 1], plo[COMP ? N : 1];
+
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            acc[a] = 0ull;
+            if (COMP) {
+                phi[a] = 0ull;
+                plo[a] = 0ull;
+            }
+        }
+    }
+
+    template <bool FIRST>
+    __device__ __forceinline__ void put(int a, u64 v) {
+        acc[a] = FIRST ? v : add2(acc[a], v);
+    }
+    template <bool FIRST>
+    __device__ __forceinline__ void put_fma(int a, u64 b, u64 y) {
+        acc[a] = FIRST ? mul2(b, y) : fma2(b, y, acc[a]);
+    }
+
+    // Add the two points (t.x, y.x, w.x), (t.y, y.y, w.y).  FIRST assigns
+    // instead of adding (the first pair of a compensated batch).
+    template <bool FIRST>
+    __device__ __forceinline__ void add_pair(u64 t, u64 y, u64 w) {
+        if (W) {
+            put<FIRST>(0, w);
+            put_fma<FIRST>(2 * M + 1, w, y);
+        } else {
+            put<FIRST>(2 * M + 1, y);
+        }
+        const u64 b1 = W ? mul2(w, t) : t;
+        put<FIRST>(1, b1);
+        put_fma<FIRST>(2 * M + 2, b1, y);
+        const u64 t2 = add2(t, t);
+        u64 bm2 = w, bm1 = b1;
+#pragma unroll
+        for (int k = 2; k <= 2 * M; ++k) {
+            const u64 bk = CHEB ? fma2(t2, bm1, neg2(bm2)) : mul2(bm1, t);
+            put<FIRST>(k, bk);
+            if (k <= M) put_fma<FIRST>(2 * M + 1 + k, bk, y);
+            bm2 = bm1;
+            bm1 = bk;
+        }
+    }
+
+    // Compensated mode: move the batch sums into the (hi, lo) pairs (TwoSum).
+    __device__ __forceinline__ void fold() {
+        if (COMP) {
+#pragma unroll
+            for (int a = K0; a < N; ++a) {
+                const u64 b = acc[a];
+                const u64 s = add2(phi[a], b);
+                const u64 bb = sub2(s, phi[a]);
+                const u64 e = add2(sub2(phi[a], sub2(s, bb)), sub2(b, bb));
+                plo[a] = add2(plo[a], e);
+                phi[a] = s;
+            }
+        }
+    }
+
+    // Final per-thread value of slot a as double-float.
+    __device__ __forceinline__ dflt result(int a) const {
+        dflt r;
+        if (a < K0) {
+            r.hi = 0.0f;
+            r.lo = 0.0f;
+        } else if (COMP) {
+            float x0, x1, l0, l1;
+            up2(phi[a], x0, x1);
+            up2(plo[a], l0, l1);
+            const dflt u = {x0, l0}, v = {x1, l1};
+            r = df_add(u, v);
+        } else {
+            float x0, x1;
+            up2(acc[a], x0, x1);
+            two_sum(x0, x1, r.hi, r.lo);
+        }
+        return r;
+    }
+};
+
+template <int M, bool W, bool CHEB>
+struct AccGenF64 {
+    static constexpr int N = 3 * M + 2;
+    double acc[N];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int a = 0; a < N; ++a) acc[a] = 0.0;
+    }
+    __device__ __forceinline__ void add_point(double t, double y, double w) {
+        if (W) {
+            acc[0] += w;
+            acc[2 * M + 1] = fma(w, y, acc[2 * M + 1]);
+        } else {
+            acc[2 * M + 1] += y;
+        }
+        const double b1 = W ? w * t : t;
+        acc[1] += b1;
+        acc[2 * M + 2] = fma(b1, y, acc[2 * M + 2]);
+        const double t2 = t + t;
+        double bm2 = W ? w : 1.0, bm1 = b1;
+#pragma unroll
+        for (int k = 2; k <= 2 * M; ++k) {
+            const double bk = CHEB ? fma(t2, bm1, -bm2) : bm1 * t;
+            acc[k] += bk;
+            if (k <= M) acc[2 * M + 1 + k] = fma(bk, y, acc[2 * M + 1 + k]);
+            bm2 = bm1;
+            bm1 = bk;
+        }
+    }
+};
+
+// Vectorised split of [b, e) for three streams: 16-byte vectors when x, y
+// (and w) start at the same offset within 16 bytes, scalar loads otherwise.
+template <int DT, bool W>
+__device__ __forceinline__ void split_range3(const void* x, const void* y, const void* w, int64_t b, int64_t e,
+                                             int64_t& head, int64_t& nvec) {
+    split_range<DT>(x, y, b, e, head, nvec);
+    if (W && nvec > 0) {
+        int64_t h2, n2;
+        split_range<DT>(x, w, b, e, h2, n2);
+        if (h2 != head || n2 != nvec) {
+            head = e - b;
+            nvec = 0;
+        }
+    }
+}
+
+// FP32 arithmetic (FP32 or BF16 storage) over [b, e), map always applied
+// (identity constants when the caller gave no interval).
+template <int M, int DT, bool COMP, bool W, bool CHEB, int UNROLL>
+__device__ __forceinline__ void accumulate_range_gen(AccGenF32<M, COMP, W, CHEB>& A, const void* x, const void* y,
+                                                     const void* w, int64_t b, int64_t e, int64_t rank,
+                                                     int64_t nthreads, float cf, float sf) {
+    constexpr int ES = Elem<DT>::kSize, PV = Elem<DT>::kPerVec;
+    int64_t head, nvec;
+    split_range3<DT, W>(x, y, w, b, e, head, nvec);
+    const u64 c2 = pk2(cf, cf), s2 = pk2(sf, sf), one2 = pk2(1.0f, 1.0f);
+    const uint4* xv = reinterpret_cast<const uint4*>(static_cast<const char*>(x) + (b + head) * ES);
+    const uint4* yv = reinterpret_cast<const uint4*>(static_cast<const char*>(y) + (b + head) * ES);
+    const uint4* wv = W ? reinterpret_cast<const uint4*>(static_cast<const char*>(w) + (b + head) * ES) : nullptr;
+    auto feed = [&](uint4 xr, uint4 yr, uint4 wr, bool first) {
+        const uint32_t xw[4] = {xr.x, xr.y, xr.z, xr.w};
+        const uint32_t yw[4] = {yr.x, yr.y, yr.z, yr.w};
+        const uint32_t ww[4] = {wr.x, wr.y, wr.z, wr.w};
+#pragma unroll
+        for (int k = 0; k < PV / 2; ++k) {
+            u64 tp, yp, wp = one2;
+            if (DT == LSEFIT_F32) {
+                tp = pk2(__uint_as_float(xw[2 * k]), __uint_as_float(xw[2 * k + 1]));
+                yp = pk2(__uint_as_float(yw[2 * k]), __uint_as_float(yw[2 * k + 1]));
+                if (W) wp = pk2(__uint_as_float(ww[2 * k]), __uint_as_float(ww[2 * k + 1]));
+            } else {
+                tp = pk2(bf16_lo(xw[k]), bf16_hi(xw[k]));
+                yp = pk2(bf16_lo(yw[k]), bf16_hi(yw[k]));
+                if (W) wp = pk2(bf16_lo(ww[k]), bf16_hi(ww[k]));
+            }
+            tp = mul2(sub2(tp, c2), s2);
+            if (COMP && first && k == 0) A.template add_pair<true>(tp, yp, wp);
+            else A.template add_pair<false>(tp, yp, wp);
+        }
+    };
+    int64_t v = rank;
+    for (; v + (UNROLL - 1) * nthreads < nvec; v += UNROLL * nthreads) {
+        uint4 xr[UNROLL], yr[UNROLL], wr[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            xr[u] = ld_stream16(xv + v + u * nthreads);
+            yr[u] = ld_stream16(yv + v + u * nthreads);
+            wr[u] = W ? ld_stream16(wv + v + u * nthreads) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) feed(xr[u], yr[u], wr[u], u == 0);
+        A.fold();
+    }
+    for (; v < nvec; v += nthreads) {
+        feed(ld_stream16(xv + v), ld_stream16(yv + v), W ? ld_stream16(wv + v) : make_uint4(0, 0, 0, 0), true);
+        A.fold();
+    }
+    // scalar points: [b, b + head) and [b + head + nvec * PV, e), the second lane empty
+    const int64_t tail0 = b + head + nvec * PV;
+    const int64_t nscalar = head + (e - tail0);
+    for (int64_t q = rank; q < nscalar; q += nthreads) {
+        const int64_t i = q < head ? b + q : tail0 + (q - head);
+        const float xs = __fmul_rn(__fsub_rn(Elem<DT>::ld(x, i), cf), sf);
+        const float ws = W ? Elem<DT>::ld(w, i) : 1.0f;
+        A.template add_pair<COMP>(pk2(xs, 0.0f), pk2(Elem<DT>::ld(y, i), 0.0f), pk2(ws, 0.0f));
+        A.fold();
+    }
+}
+
+// FP64 arithmetic for any storage.
+template <int M, int DT, bool W, bool CHEB, int UNROLL>
+__device__ __forceinline__ void accumulate_range_gen_f64(AccGenF64<M, W, CHEB>& A, const void* x, const void* y,
+                                                         const void* w, int64_t b, int64_t e, int64_t rank,
+                                                         int64_t nthreads, double c, double s) {
+    constexpr int ES = Elem<DT>::kSize, PV = Elem<DT>::kPerVec;
+    int64_t head, nvec;
+    split_range3<DT, W>(x, y, w, b, e, head, nvec);
+    const uint4* xv = reinterpret_cast<const uint4*>(static_cast<const char*>(x) + (b + head) * ES);
+    const uint4* yv = reinterpret_cast<const uint4*>(static_cast<const char*>(y) + (b + head) * ES);
+    const uint4* wv = W ? reinterpret_cast<const uint4*>(static_cast<const char*>(w) + (b + head) * ES) : nullptr;
+    auto feed = [&](uint4 xr, uint4 yr, uint4 wr) {
+        double xs[PV], ys[PV], ws[PV];
+        unpack_f64<DT, PV>(xr, xs);
+        unpack_f64<DT, PV>(yr, ys);
+        if (W) unpack_f64<DT, PV>(wr, ws);
+#pragma unroll
+        for (int q = 0; q < PV; ++q) A.add_point(s * (xs[q] - c), ys[q], W ? ws[q] : 1.0);
+    };
+    int64_t v = rank;
+    for (; v + (UNROLL - 1) * nthreads < nvec; v += UNROLL * nthreads) {
+        uint4 xr[UNROLL], yr[UNROLL], wr[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            xr[u] = ld_stream16(xv + v + u * nthreads);
+            yr[u] = ld_stream16(yv + v + u * nthreads);
+            wr[u] = W ? ld_stream16(wv + v + u * nthreads) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) feed(xr[u], yr[u], wr[u]);
+    }
+    for (; v < nvec; v += nthreads)
+        feed(ld_stream16(xv + v), ld_stream16(yv + v), W ? ld_stream16(wv + v) : make_uint4(0, 0, 0, 0));
+    const int64_t tail0 = b + head + nvec * PV;
+    const int64_t nscalar = head + (e - tail0);
+    for (int64_t q = rank; q < nscalar; q += nthreads) {
+        const int64_t i = q < head ? b + q : tail0 + (q - head);
+        A.add_point(s * (Elem<DT>::ld64(x, i) - c), Elem<DT>::ld64(y, i), W ? Elem<DT>::ld64(w, i) : 1.0);
+    }
+}
+
+// Monomial coefficients of sum_k a_k T_k(t) (k <= m): the recurrence of the
+// basis applied to coefficient rows, P_{k+1}(t) = 2 t P_k(t) - P_{k-1}(t).
+template <int NMAX>
+__device__ __forceinline__ void cheb_to_mono(int m, const double* a, double* out) {
+    constexpr int N = NMAX + 1;
+    double pm1[N], p[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        pm1[j] = j == 0 ? 1.0 : 0.0;
+        p[j] = j == 1 ? 1.0 : 0.0;
+        out[j] = a[0] * pm1[j] + (m >= 1 ? a[1] * p[j] : 0.0);
+    }
+#pragma unroll
+    for (int k = 2; k < N; ++k) {
+        if (k > m) break;
+#pragma unroll
+        for (int j = N - 1; j >= 0; --j) {
+            const double nj = (j > 0 ? 2.0 * p[j - 1] : 0.0) - pm1[j];
+            pm1[j] = p[j];
+            p[j] = nj;
+            out[j] = fma(a[k], nj, out[j]);
+        }
+    }
+}
+
+// Solve of the generalised normal equations from the moments Mo[0..2m] and
+// right-hand sides T[0..m] (count = number of points).  Monomial basis:
+// G[j][k] = Mo[j+k]; Chebyshev: G[j][k] = (Mo[j+k] + Mo[|j-k|]) / 2.
+// Singular when a pivot is at or below (m+1) * eps * max|G|.  Writes Xb (the
+// coefficients in the basis of t) and X (monomials of x), NaN on failure.
+template <int NMAX, bool CHEB>
+__device__ int solve_general_rt(int m, const double* Mo, const double* T, double count, double c, double s,
+                                bool map_ok, double eps, double* Xb, double* X, int ncoef) {
+    constexpr int N = NMAX + 1;
+    int st = LSEFIT_OK;
+    if (!map_ok) st = LSEFIT_ERR_BAD_INTERVAL;
+    else if (!(count >= (double)(m + 1))) st = LSEFIT_ERR_N_TOO_SMALL;
+    if (st == LSEFIT_OK) {
+        bool fin = true;
+        for (int k = 0; k <= 2 * m; ++k) fin = fin && isfinite(Mo[k]);
+        for (int k = 0; k <= m; ++k) fin = fin && isfinite(T[k]);
+        if (!fin) st = LSEFIT_ERR_NONFINITE;
+    }
+    double z[N];
+    if (st == LSEFIT_OK) {
+        double A[N][N + 1];
+        double amax = 0.0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                double g = (j == k) ? 1.0 : 0.0;
+                if (j <= m && k <= m) {
+                    g = CHEB ? 0.5 * (Mo[j + k] + Mo[j > k ? j - k : k - j]) : Mo[j + k];
+                    amax = fmax(amax, fabs(g));
+                }
+                A[j][k] = g;
+            }
+            A[j][N] = (j <= m) ? T[j] : 0.0;
+        }
+        st = ge_padded<NMAX>(m, A, (double)(m + 1) * eps * amax, z);
+    }
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    if (st != LSEFIT_OK) {
+        for (int i = 0; i < ncoef; ++i) {
+            const double v = i <= m ? qnan : 0.0;
+            if (Xb) Xb[i] = v;
+            X[i] = v;
+        }
+        return st;
+    }
+    double zt[N], out[N];
+    if (CHEB) {
+        cheb_to_mono<NMAX>(m, z, zt);
+    } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j) zt[j] = z[j];
+    }
+    unmap_padded<NMAX>(m, zt, c, s, out);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (i < ncoef) {
+            if (Xb) Xb[i] = i <= m ? z[i] : 0.0;
+            X[i] = i <= m ? out[i] : 0.0;
+        }
+    }
+    for (int i = N; i < ncoef; ++i) {
+        if (Xb) Xb[i] = 0.0;
+        X[i] = 0.0;
+    }
+    return LSEFIT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Single-series kernels (as the power-sum pass: per-block partials in FP64,
+// the last block combines them in a fixed order and solves).
+// ---------------------------------------------------------------------------
+constexpr int kGenBlock = 256;
+
+struct GenParams {
+    const void* x;
+    const void* y;
+    const void* w;
+    int64_t n;
+    const double* interval;
+    double* sums;           // [3m+2] or null: M_0..M_2m, T_0..T_m
+    double* map_out;        // [2] or null
+    double* partials;       // [gridDim.x][3m+2]
+    unsigned int* ticket;   // zero between calls
+    int m_lo;
+    double eps;
+    double* X;              // [m-m_lo+1][m+1]
+    double* Xb;             // same shape or null
+    int32_t* status;        // [m-m_lo+1]
+};
+
+template <int M, bool W, bool CHEB>
+__device__ __noinline__ void gen_solve_degree(const GenParams& p, const double* tot, double c, double s,
+                                              bool map_ok, int lane) {
+    const int d = p.m_lo + lane;
+    p.status[lane] = solve_general_rt<M, CHEB>(d, tot, tot + 2 * M + 1, (double)p.n, c, s, map_ok, p.eps,
+                                               p.Xb ? p.Xb + lane * (M + 1) : nullptr, p.X + lane * (M + 1), M + 1);
+}
+
+template <int M, bool W, bool CHEB>
+__device__ void gen_publish(const GenParams& p, const double* blk, bool map_ok, double c, double s) {
+    constexpr int N = 3 * M + 2;
+    constexpr int J = kGenBlock / N;
+    __shared__ bool s_last;
+    __shared__ double comb[kGenBlock];
+    __shared__ double tot_s[N];
+    const int tid = threadIdx.x;
+    if (tid < N) {
+        p.partials[(size_t)blockIdx.x * N + tid] = blk[tid];
+        __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(p.ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int G = gridDim.x;
+    if (tid < N * J) {
+        const int a = tid / J, j = tid % J;
+        double v = 0.0;
+        for (int b = j; b < G; b += J) v += __ldcg(p.partials + (size_t)b * N + a);
+        comb[tid] = v;
+    }
+    __syncthreads();
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    if (tid < N) {
+        double tot = 0.0;
+        for (int j = 0; j < J; ++j) tot += comb[tid * J + j];
+        if (tid == 0 && !W) tot = (double)p.n;
+        tot_s[tid] = map_ok ? tot : qnan;
+        if (p.sums) p.sums[tid] = map_ok ? tot : qnan;
+    }
+    if (tid == 0) {
+        if (p.map_out) {
+            p.map_out[0] = map_ok ? c : qnan;
+            p.map_out[1] = map_ok ? s : qnan;
+        }
+        *p.ticket = 0u;  // ready for the next call
+    }
+    __syncthreads();
+    if (tid < 32 && tid <= M - p.m_lo) gen_solve_degree<M, W, CHEB>(p, tot_s, c, s, map_ok, tid);
+}
+
+template <int M, int DT, bool COMP, bool W, bool CHEB, int UNROLL>
+__global__ void __launch_bounds__(kGenBlock) gen_kernel_f32(GenParams p) {
+    constexpr int N = 3 * M + 2;
+    __shared__ dflt red[(kGenBlock / 32) * kGenBlock];
+    __shared__ double blk[N];
+    double cd, sd;
+    const bool map_ok = map_constants(p.interval, true, cd, sd);
+    AccGenF32<M, COMP, W, CHEB> A;
+    A.init();
+    const int64_t nthr = (int64_t)gridDim.x * kGenBlock;
+    const int64_t gtid = (int64_t)blockIdx.x * kGenBlock + threadIdx.x;
+    accumulate_range_gen<M, DT, COMP, W, CHEB, UNROLL>(A, p.x, p.y, p.w, 0, p.n, gtid, nthr, (float)cd, (float)sd);
+    block_reduce_df<kGenBlock, N>([&](int a) { return A.result(a); }, red, blk);
+    gen_publish<M, W, CHEB>(p, blk, map_ok, cd, sd);
+}
+
+template <int M, int DT, bool W, bool CHEB, int UNROLL>
+__global__ void __launch_bounds__(kGenBlock) gen_kernel_f64(GenParams p) {
+    constexpr int N = 3 * M + 2;
+    __shared__ double red[(kGenBlock / 32) * kGenBlock];
+    __shared__ double blk[N];
+    double c, s;
+    const bool map_ok = map_constants(p.interval, false, c, s);
+    AccGenF64<M, W, CHEB> A;
+    A.init();
+    const int64_t nthr = (int64_t)gridDim.x * kGenBlock;
+    const int64_t gtid = (int64_t)blockIdx.x * kGenBlock + threadIdx.x;
+    accumulate_range_gen_f64<M, DT, W, CHEB, UNROLL>(A, p.x, p.y, p.w, 0, p.n, gtid, nthr, c, s);
+    block_reduce_d<kGenBlock, N>([&](int a) { return A.acc[a]; }, red, blk);
+    gen_publish<M, W, CHEB>(p, blk, map_ok, c, s);
+}
+
+typedef void (*gen_kernel_t)(GenParams);
+
+// Kernel for degree M, storage, accumulation and kind.
+template <int M, bool W, bool CHEB>
+gen_kernel_t gen_pick_m(int dtype, int accum) {
+    constexpr int U = W ? 2 : (M <= 4 ? 4 : 2);
+    if (accum == LSEFIT_ACCUM_F64) {
+        if (dtype == LSEFIT_F64) return gen_kernel_f64<M, LSEFIT_F64, W, CHEB, 2>;
+        if (dtype == LSEFIT_F32) return gen_kernel_f64<M, LSEFIT_F32, W, CHEB, 2>;
+        return gen_kernel_f64<M, LSEFIT_BF16, W, CHEB, 1>;
+    }
+    if (dtype == LSEFIT_F64) return nullptr;
+    const bool comp = accum == LSEFIT_ACCUM_COMP;
+    if (dtype == LSEFIT_F32)
+        return comp ? gen_kernel_f32<M, LSEFIT_F32, true, W, CHEB, U> : gen_kernel_f32<M, LSEFIT_F32, false, W, CHEB, U>;
+    return comp ? gen_kernel_f32<M, LSEFIT_BF16, true, W, CHEB, 2> : gen_kernel_f32<M, LSEFIT_BF16, false, W, CHEB, 2>;
+}
+
+template <bool W, bool CHEB>
+gen_kernel_t gen_pick(int m, int dtype, int accum) {
+    switch (m) {
+        case 1: return gen_pick_m<1, W, CHEB>(dtype, accum);
+        case 2: return gen_pick_m<2, W, CHEB>(dtype, accum);
+        case 3: return gen_pick_m<3, W, CHEB>(dtype, accum);
+        case 4: return gen_pick_m<4, W, CHEB>(dtype, accum);
+        case 5: return gen_pick_m<5, W, CHEB>(dtype, accum);
+        case 6: return gen_pick_m<6, W, CHEB>(dtype, accum);
+        case 7: return gen_pick_m<7, W, CHEB>(dtype, accum);
+        default: return gen_pick_m<8, W, CHEB>(dtype, accum);
+    }
+}
+
+// One translation unit per kind instantiates its kernels.
+gen_kernel_t gen_pick_weighted(int m, int dtype, int accum);
+gen_kernel_t gen_pick_chebyshev(int m, int dtype, int accum);
+gen_kernel_t gen_pick_weighted_chebyshev(int m, int dtype, int accum);
+
+}  // namespace lsefit

@@ -22,6 +22,11 @@ int current_sm_count(int* device_out);
 // shared memory (cached per kernel).  Returns at least 1.
 int occupancy_blocks(const void* kernel, int threads, size_t smem);
 
+// Device address of a point array: device or managed memory as is; host
+// memory only when registered with CUDA (pinned), through the address CUDA
+// reports for it.  Unregistered host memory gives LSEFIT_ERR_INVALID_ARG.
+int resolve_device_pointer(const void*& ptr);
+
 inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 inline int elem_size(int dtype) { return dtype == 0 ? 8 : (dtype == 1 ? 4 : 2); }

@@ -184,23 +184,6 @@ static ps_kernel_t pick_kernel(int m, int dtype, int accum, bool map) {
     }
 }
 
-// Device address of a point array: device/managed memory as is; host memory
-// only when it is registered with CUDA (pinned), through the address CUDA
-// reports for it.  Unregistered host memory is rejected.
-static int resolve_points(const void*& ptr) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return LSEFIT_ERR_INVALID_ARG;
-    }
-    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return LSEFIT_OK;
-    if (a.type == cudaMemoryTypeHost && a.devicePointer != nullptr) {
-        ptr = a.devicePointer;
-        return LSEFIT_OK;
-    }
-    return LSEFIT_ERR_INVALID_ARG;
-}
-
 }  // namespace lsefit
 
 using namespace lsefit;
@@ -226,7 +209,7 @@ static int launch_powersums(const void* x, const void* y, int64_t n, int dtype, 
     if (workspace_bytes < lsefit_powersums_workspace_size(m)) return LSEFIT_ERR_WORKSPACE;
 
     if (n > 0) {
-        if (resolve_points(x) != LSEFIT_OK || resolve_points(y) != LSEFIT_OK) return LSEFIT_ERR_INVALID_ARG;
+        if (resolve_device_pointer(x) != LSEFIT_OK || resolve_device_pointer(y) != LSEFIT_OK) return LSEFIT_ERR_INVALID_ARG;
     }
     const int es = elem_size(dtype);
     const int per_vec = 16 / es;

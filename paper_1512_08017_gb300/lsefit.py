@@ -90,6 +90,9 @@ SIGNATURES = {
     "lsefit_solve_cholesky": (_INT, [_VP, _I64, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP]),
     "lsefit_fit": (_INT, [_VP, _VP, _I64, _INT, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "lsefit_fit_noalloc_scratch_bytes": (_SZ, []),
+    "lsefit_fit_general_workspace_size": (_SZ, [_INT]),
+    "lsefit_fit_general": (_INT, [_VP, _VP, _VP, _I64, _INT, _INT, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP, _VP,
+                                  _VP, _SZ, _VP]),
     "lsefit_fit_noalloc": (_INT, [_VP, _VP, _I64, _INT, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "lsefit_plan_build": (_INT, [_VP, _VP, _I64, _INT, _VP, _INT, _VP, _VP, _I64, _VP, _I64]),
     "lsefit_batched_workspace_size": (_SZ, [_VP]),
@@ -292,6 +295,50 @@ def fit_degrees(x: torch.Tensor, y: torch.Tensor, m: int, m_lo: int = 1, accum="
                         _ptr(iv), _ptr(out["X"]), _ptr(out.get("Xt")), _ptr(out.get("sums")),
                         _ptr(out.get("map")), _ptr(out["status"]), _ptr(ws), ws.numel(), ctypes.c_void_p(sh))
     _check(rc, "lsefit_fit")
+    return out
+
+
+BASES = {"monomial": 0, "chebyshev": 1}
+
+
+def fit_general(x: torch.Tensor, y: torch.Tensor, m: int, w: torch.Tensor | None = None, basis: str = "monomial",
+                m_lo: int | None = None, accum="comp", interval=None, *, out: dict | None = None,
+                stream=None) -> dict:
+    """Weighted and/or Chebyshev-basis fit of one series (lsefit_fit_general):
+    minimises sum_i w_i (y_i - f(t_i))^2, f = sum_k Xb[k] phi_k(t), phi_k = t^k
+    or T_k(t).  Degrees m_lo..m (default m alone) from one pass.
+
+    Returns dict(X [k, m+1] monomials of x, Xb [k, m+1] basis coefficients,
+    sums [3m+2], map [2], status [k]) with k = m - m_lo + 1."""
+    if x.dim() != 1 or x.shape != y.shape or x.dtype != y.dtype:
+        raise ValueError("x and y must be 1-D tensors of the same shape and dtype")
+    if w is not None and (w.shape != x.shape or w.dtype != x.dtype):
+        raise ValueError("w must have the shape and dtype of x")
+    for t in (x, y) + ((w,) if w is not None else ()):
+        if not (t.is_cuda or t.is_pinned()):
+            raise ValueError("x, y and w must be CUDA tensors or pinned host tensors")
+    if basis not in BASES:
+        raise ValueError(f"basis must be one of {sorted(BASES)}")
+    m_lo = m if m_lo is None else m_lo
+    if not (1 <= m_lo <= m <= MAX_DEGREE):
+        raise ValueError(f"need 1 <= m_lo <= m <= {MAX_DEGREE}")
+    dev = _device_of(x)
+    sh = _stream_handle(stream)
+    iv = _interval_tensor(interval, dev)
+    k = m - m_lo + 1
+    if out is None:
+        out = {"X": torch.empty(k, m + 1, dtype=torch.float64, device=dev),
+               "Xb": torch.empty(k, m + 1, dtype=torch.float64, device=dev),
+               "sums": torch.empty(3 * m + 2, dtype=torch.float64, device=dev),
+               "map": torch.empty(2, dtype=torch.float64, device=dev),
+               "status": torch.empty(k, dtype=torch.int32, device=dev)}
+    # the general pass and lsefit_fit both leave the workspace's ticket zeroed: one buffer serves both
+    ws = workspace("powersums", lib.lsefit_fit_general_workspace_size(m), dev, sh)
+    rc = lib.lsefit_fit_general(_ptr(x), _ptr(y), _ptr(w), x.numel(), _dtype_code(x), int(m), int(m_lo),
+                                _accum_code(accum), BASES[basis], _ptr(iv), _ptr(out["X"]), _ptr(out.get("Xb")),
+                                _ptr(out.get("sums")), _ptr(out.get("map")), _ptr(out["status"]), _ptr(ws),
+                                ws.numel(), ctypes.c_void_p(sh))
+    _check(rc, "lsefit_fit_general")
     return out
 
 

@@ -39,6 +39,7 @@ SEED_SINGLE_LARGE = 1513
 SEED_RAGGED = 1514
 SEED_DIFF = 1515
 SEED_PRECISION = 1516
+SEED_WEIGHTS = 1517
 
 TRUE_SINGLE_FP64 = (1.5, -0.8, 0.3, -0.02)
 
@@ -106,6 +107,25 @@ def single_large(n: int = 1 << 28, m: int = 3, seed: int = SEED_SINGLE_LARGE,
     with ThreadPoolExecutor(threads or _threads()) as ex:
         list(ex.map(work, range(nchunks)))
     return {"x": x[:n], "y": y[:n], "true": coef}
+
+
+def weights(n: int, seed: int = SEED_WEIGHTS, lo: float = 0.1, hi: float = 3.0,
+            out: np.ndarray | None = None, threads: int | None = None) -> np.ndarray:
+    """Per-point weights w ~ U[lo, hi], FP32, drawn in chunks of 2^22 (``out``
+    may be a preallocated FP32 buffer of length n)."""
+    nchunks = (n + CHUNK - 1) // CHUNK
+    kids = np.random.SeedSequence(seed).spawn(max(nchunks, 1))
+    w = out if out is not None else np.empty(n, dtype=np.float32)
+    assert w.dtype == np.float32 and w.size >= n
+
+    def work(ci):
+        a = ci * CHUNK
+        b = min(n, a + CHUNK)
+        w[a:b] = np.random.default_rng(kids[ci]).uniform(lo, hi, b - a).astype(np.float32)
+
+    with ThreadPoolExecutor(threads or _threads()) as ex:
+        list(ex.map(work, range(nchunks)))
+    return w[:n]
 
 
 def ragged_lengths(num_series: int, lmin: int, lmax: int, rng) -> np.ndarray:
