@@ -300,14 +300,17 @@ typedef struct lsefit_tuning {
                                  1 = longest first; 2 (0 = default) = grouped by degree
                                  when degrees are given, longest first within a degree */
     int32_t schedule;         /* how warps take warp tasks:
-                                 1 = from one atomic queue, in plan order;
+                                 1 = from one queue, in plan order;
                                  2 = fixed snake order (round r gives warp w task r*W + w,
                                      or r*W + W-1-w on odd rounds; W warps in the grid);
                                  3 (0 = default) = one queue per degree class, longest
                                      first; every block starts on a class (blocks shared
                                      out in proportion to the classes' points) and moves
                                      to the next class with tasks left when its class runs
-                                     dry, so the warps of an SM run the code of one degree */
+                                     dry, so the warps of an SM run the code of one degree.
+                                 In 1 and 3 a warp's first three tasks of its first queue
+                                 are snake rounds over that queue's warps; later tasks
+                                 come from an atomic counter. */
     int32_t reserved[2];
 } lsefit_tuning;
 

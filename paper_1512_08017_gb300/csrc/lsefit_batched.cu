@@ -200,7 +200,6 @@ extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* 
     p.total_points = plan->total_points;
     p.sched = plan->tuning.schedule;
     for (int c = 0; c <= kClasses; ++c) p.cls_begin[c] = plan->class_begin[c];
-    for (int c = 0; c < kClasses; ++c) p.cls_points[c] = plan->class_points[c];
     p.X = X;
     p.Xt = Xt;
     p.sums = sums;
@@ -239,6 +238,24 @@ extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* 
     const int64_t useful = (int64_t)plan->n_block_tasks + (plan->n_warp_tasks + kBWarps - 1) / kBWarps;
     if (useful < grid) grid = useful;
     if (grid < 1) grid = 1;
+    // schedule 3: blocks shared out over the degree classes in proportion to
+    // their points (block b starts on the class holding (b + 1/2) / grid of them)
+    {
+        double total = 0.0;
+        for (int c = 0; c < kClasses; ++c) total += (double)plan->class_points[c];
+        int c = 0;
+        double cum = (double)plan->class_points[0];
+        p.cls_block[0] = 0;
+        for (int64_t blk = 0; blk < grid; ++blk) {
+            const double target = ((double)blk + 0.5) / (double)grid * total;
+            while (c < kClasses - 1 && !(cum > target)) {
+                ++c;
+                cum += (double)plan->class_points[c];
+                p.cls_block[c] = (int)blk;
+            }
+        }
+        for (int k = c + 1; k <= kClasses; ++k) p.cls_block[k] = (int)grid;
+    }
     {
         const int pt = 256;
         const int64_t items = std::max<int64_t>(std::max<int64_t>(b.num_series, plan->n_block_tasks), kCounters);

@@ -57,8 +57,8 @@ struct BParams {
     int n_warp_tasks;
     int64_t total_points;
     int sched;             // 1 one queue, 2 snake order, 3 degree classes
-    int cls_begin[LSEFIT_MAX_DEGREE + 2];        // warp tasks of class c: [cls_begin[c], cls_begin[c+1])
-    long long cls_points[LSEFIT_MAX_DEGREE + 1];  // points of class c
+    int cls_begin[LSEFIT_MAX_DEGREE + 2];  // warp tasks of class c: [cls_begin[c], cls_begin[c+1])
+    int cls_block[LSEFIT_MAX_DEGREE + 2];  // blocks starting on class c: [cls_block[c], cls_block[c+1])
     double* X;
     double* Xt;
     double* sums;
@@ -131,17 +131,21 @@ struct PendLayout {
     static constexpr size_t kWarpBytes = (size_t)32 * kStride * 8 + 32 * 4 * 2;
 };
 
+// A warp's queue of finished series.  The entry count n is warp-uniform
+// register state, updated identically by every lane of the owning warp (no
+// lane ever waits on another lane's store to learn it); it is published to
+// shared memory only for the block's final consolidated solve.
 template <int NMAX>
 struct Pend {
     unsigned long long* row;  // [32][kStride] 8-byte words (global workspace)
     int* sid;                 // [32] series id (global workspace)
     int* meta;                // [32] degree (global workspace)
-    int* count;               // [1] (shared memory)
-    __device__ __forceinline__ void bind(unsigned char* base, int* cnt) {
+    int n;                    // entries queued
+    __device__ __forceinline__ void bind(unsigned char* base) {
         row = reinterpret_cast<unsigned long long*>(base);
         sid = reinterpret_cast<int*>(base + 32 * PendLayout<NMAX>::kStride * 8);
         meta = sid + 32;
-        count = cnt;
+        n = 0;
     }
 };
 
@@ -210,17 +214,22 @@ struct Ring {
     }
 };
 
-// Producer cursor of a warp.  Warp tasks come from one atomic queue in plan
-// order (warps that drew long series simply take fewer), from a fixed snake
-// order (round r gives warp w task r*W + w, or r*W + W-1-w on odd rounds, W
-// warps in the grid), or from one queue per degree class: a block starts on
-// the class its index falls in when the blocks are shared out in proportion
-// to the classes' points, and a warp whose class has run dry moves on to the
-// next class with tasks left, so the warps of an SM keep running the code of
-// one degree.  Three tasks are in the pipeline ahead of the one being issued,
-// one step per advance, so no advance waits on a load: tq (lane 0) holds the
-// next index, a (lane 0) the task record loaded for the index before, b (all
-// lanes) a record with its degree and map constants loaded.
+// Producer cursor of a warp.  Warp tasks are drawn from one queue in plan
+// order (schedule 1), in a fixed snake order (schedule 2: round r gives warp
+// w task r*W + w, or r*W + W-1-w on odd rounds, W warps in the grid), or
+// from one queue per degree class (schedule 3): a block starts on the class
+// its index falls in when the blocks are shared out in proportion to the
+// classes' points (cls_block, set at launch), and a warp whose class has run
+// dry moves on to the next class with tasks left, so the warps of an SM keep
+// running the code of one degree.  In schedules 1 and 3 the first
+// kStaticRounds draws of a warp are fixed snake rounds over the warps of its
+// first queue and only later draws take an atomic ticket (offset past the
+// static rounds): a grid that starts with every warp hitting one counter
+// spends microseconds in its queue.  Three tasks are in the pipeline ahead
+// of the one being issued, one step per advance, so no advance waits on a
+// load: tq (lane 0) holds the next index, a (lane 0) the task record loaded
+// for the index before, b (all lanes) a record with its degree and map
+// constants loaded.
 struct Cursor {
     bool have;
     int s, deg;
@@ -234,60 +243,59 @@ struct Cursor {
     int at;     // lane 0: task index of slot a (>= n_warp_tasks: none)
     int4 arec;  // lane 0: record of slot a
     int tq;     // lane 0: next task index
-    int round;  // lane 0: snake round of the next index
-    int cls;    // lane 0: degree class drawn from
+    int round;  // lane 0: snake round of the next index (static rounds while < kStaticRounds)
+    int cls;    // lane 0: queue drawn from (degree class; 0 in schedule 1)
 };
 
-__device__ __forceinline__ int cursor_draw(Cursor& cu, const BParams& p) {
+constexpr int kStaticRounds = 3;
+
+// Returns {task index (kNone: no work left), round, queue} for the draw made
+// in state (round, cls).  Out of line, with the state passed by value, so the
+// cursor itself stays in registers.
+static __device__ __noinline__ int3 cursor_draw(int round, int cls, const BParams& p) {
     constexpr int kNone = 0x7fffffff;
+    const int warp = threadIdx.x >> 5;
     if (p.sched == 2) {
         const long long nw = (long long)gridDim.x * kBWarps;
-        const long long wid = (long long)blockIdx.x * kBWarps + (threadIdx.x >> 5);
-        const long long t = (long long)cu.round * nw + ((cu.round & 1) ? (nw - 1 - wid) : wid);
-        cu.round++;
-        return t < p.n_warp_tasks ? (int)t : kNone;
+        const long long wid = (long long)blockIdx.x * kBWarps + warp;
+        const long long t = (long long)round * nw + ((round & 1) ? (nw - 1 - wid) : wid);
+        round++;
+        return make_int3(t < p.n_warp_tasks ? (int)t : kNone, round, cls);
     }
-    if (p.sched != 3) return (int)atomicAdd(&p.counters[1], 1u);
-    // every class is tried at most once; a class stays behind once it runs dry
-    for (int tries = 0; tries < kClasses; ++tries) {
-        const int c = cu.cls;
-        const int b = p.cls_begin[c], n = p.cls_begin[c + 1] - b;
-        if (n > 0) {
-            const unsigned k = atomicAdd(&p.counters[3 + c], 1u);
-            if (k < (unsigned)n) return b + (int)k;
+    const bool classes = p.sched == 3;
+    // every queue is visited at most once per draw; a queue stays behind once it runs dry
+    for (int tries = 0; tries <= kClasses; ++tries) {
+        const int c = cls;
+        const int b = classes ? p.cls_begin[c] : 0;
+        const int n = classes ? p.cls_begin[c + 1] - b : p.n_warp_tasks;
+        const int blk0 = classes ? p.cls_block[c] : 0;
+        const int nwc = (classes ? p.cls_block[c + 1] - blk0 : (int)gridDim.x) * kBWarps;
+        const int nstatic = min(n, kStaticRounds * nwc);
+        if (round < kStaticRounds) {  // the warp's first queue: fixed snake rounds
+            const int r = ((int)blockIdx.x - blk0) * kBWarps + warp;
+            const int local = round * nwc + ((round & 1) ? (nwc - 1 - r) : r);
+            round++;
+            if (local < nstatic) return make_int3(b + local, round, cls);
+            round = kStaticRounds;
         }
-        cu.cls = c + 1 == kClasses ? 0 : c + 1;
+        if (n > nstatic) {
+            const unsigned k = atomicAdd(&p.counters[classes ? 3 + c : 1], 1u);
+            if (k < (unsigned)(n - nstatic)) return make_int3(b + nstatic + (int)k, round, cls);
+        }
+        if (!classes) return make_int3(kNone, round, cls);
+        cls = c + 1 == kClasses ? 0 : c + 1;
+        round = kStaticRounds;
     }
-    return kNone;
+    return make_int3(kNone, round, cls);
 }
 
-// First class of a block: blocks shared out over the classes in proportion
-// to their points.
+// First queue of this block's warps: the degree class whose block range holds
+// blockIdx.x (schedule 3), else the single queue.
 __device__ __forceinline__ int first_class(const BParams& p) {
-    long long total = 0;
-    for (int c = 0; c < kClasses; ++c) total += p.cls_points[c];
-    if (total <= 0) return 0;
-    const double target = ((double)blockIdx.x + 0.5) / (double)gridDim.x * (double)total;
-    long long cum = 0;
-    for (int c = 0; c < kClasses; ++c) {
-        cum += p.cls_points[c];
-        if ((double)cum > target) return c;
-    }
-    return kClasses - 1;
-}
-
-__device__ __forceinline__ void cursor_init(Cursor& cu, const BParams& p) {
-    cu.have = false;
-    cu.bv = false;
-    cu.at = 0x7fffffff;
-    cu.arec = make_int4(0, 0, 0, 0);
-    cu.tq = 0x7fffffff;
-    cu.round = 0;
-    cu.cls = 0;
-    if ((threadIdx.x & 31) == 0) {
-        if (p.sched == 3) cu.cls = first_class(p);
-        cu.tq = cursor_draw(cu, p);
-    }
+    if (p.sched != 3) return 0;
+    for (int c = 0; c < kClasses; ++c)
+        if ((int)blockIdx.x < p.cls_block[c + 1]) return c;
+    return 0;
 }
 
 // One step of the pipeline: b becomes current, a moves to b (loading degree
@@ -318,29 +326,62 @@ __device__ __forceinline__ void cursor_step(Cursor& cu, const BParams& p) {
         cu.at = cu.tq;
         if (cu.tq < p.n_warp_tasks) {
             cu.arec = p.warp_tasks[cu.tq];
-            cu.tq = cursor_draw(cu, p);
+            const int3 d = cursor_draw(cu.round, cu.cls, p);
+            cu.tq = d.x;
+            cu.round = d.y;
+            cu.cls = d.z;
         }
     }
+}
+
+// Status and NaN row of the cursor's current task, whose degree is outside
+// 1..m_max: it is not fitted at all and gets no stages (lane 0 writes).
+__device__ __forceinline__ void mark_invalid_task(const Cursor& cu, const BParams& p) {
+    if ((threadIdx.x & 31) == 0) {
+        const int64_t s = cu.s;
+        const int nc = p.m_max + 1;
+        const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+        for (int i = 0; i < nc; ++i) {
+            p.X[s * nc + i] = qnan;
+            if (p.Xt) p.Xt[s * nc + i] = qnan;
+        }
+        if (p.sums)
+            for (int k = 0; k < 3 * p.m_max + 2; ++k) p.sums[s * (3 * p.m_max + 2) + k] = qnan;
+        p.status[s] = LSEFIT_ERR_INVALID_ARG;
+    }
+}
+
+__device__ __forceinline__ bool cursor_valid_degree(const Cursor& cu, const BParams& p) {
+    return cu.deg >= 1 && cu.deg <= p.m_max;
 }
 
 __device__ __forceinline__ void cursor_advance(Cursor& cu, const BParams& p) {
     for (;;) {
         cursor_step(cu, p);
-        if (!cu.have || (cu.deg >= 1 && cu.deg <= p.m_max)) return;
-        // not fitted at all: status and NaN row, no stages
-        if ((threadIdx.x & 31) == 0) {
-            const int64_t s = cu.s;
-            const int nc = p.m_max + 1;
-            const double qnan = __longlong_as_double(0x7ff8000000000000ll);
-            for (int i = 0; i < nc; ++i) {
-                p.X[s * nc + i] = qnan;
-                if (p.Xt) p.Xt[s * nc + i] = qnan;
-            }
-            if (p.sums)
-                for (int k = 0; k < 3 * p.m_max + 2; ++k) p.sums[s * (3 * p.m_max + 2) + k] = qnan;
-            p.status[s] = LSEFIT_ERR_INVALID_ARG;
-        }
+        if (!cu.have || cursor_valid_degree(cu, p)) return;
+        mark_invalid_task(cu, p);
     }
+}
+
+// Start of phase 2: the first draw, then one pipeline step per prefetch slot
+// (index -> a -> b -> current).
+__device__ __forceinline__ void cursor_init(Cursor& cu, const BParams& p) {
+    cu.have = false;
+    cu.bv = false;
+    cu.at = 0x7fffffff;
+    cu.arec = make_int4(0, 0, 0, 0);
+    cu.tq = 0x7fffffff;
+    cu.round = 0;
+    cu.cls = 0;
+    if ((threadIdx.x & 31) == 0) {
+        const int3 d = cursor_draw(0, first_class(p), p);
+        cu.tq = d.x;
+        cu.round = d.y;
+        cu.cls = d.z;
+    }
+    cursor_step(cu, p);     // index -> a
+    cursor_step(cu, p);     // a -> b
+    cursor_advance(cu, p);  // b -> current
 }
 
 template <int ES>
@@ -415,43 +456,76 @@ __device__ __forceinline__ void ring_wait(int pending) {
 }
 
 // Solve one queued series (entry idx of warp ws's queue in this block), if
-// `active`.  Converts the entry's sums to FP64 in place.
+// `active`.  Called by all 32 lanes of a warp together (the degree and map
+// votes below span the full warp).  Converts the entry's sums to FP64 in place.
 template <int NMAX, int ACC>
 __device__ __noinline__ void pend_solve_entry(const BParams& p, unsigned char* pend_block, int ws, int idx,
                                               bool active) {
-    if (!active) return;
     constexpr int W = PendLayout<NMAX>::kStride;
-    unsigned char* base = pend_block + (size_t)ws * PendLayout<NMAX>::kWarpBytes;
-    unsigned long long* row = reinterpret_cast<unsigned long long*>(base) + (size_t)idx * W;
-    const int* sid = reinterpret_cast<const int*>(base + 32 * W * 8);
-    const int m = sid[32 + idx];
-    const int64_t s = sid[idx];
-    const int ns = 3 * m + 2;
-    double* sm = reinterpret_cast<double*>(row);
-    sm[0] = (double)(long long)row[0];
-    if (ACC != LSEFIT_ACCUM_F64) {
-        for (int k = 1; k < ns; ++k) {
-            const dflt v = bits_df(row[k]);
-            sm[k] = f32_to_f64_int(v.hi) + f32_to_f64_int(v.lo);
+    int m = 0;
+    int64_t s = 0;
+    double c = 0.0, sc = 1.0;
+    bool ok = false;
+    double* sm = nullptr;
+    if (active) {
+        unsigned char* base = pend_block + (size_t)ws * PendLayout<NMAX>::kWarpBytes;
+        unsigned long long* row = reinterpret_cast<unsigned long long*>(base) + (size_t)idx * W;
+        const int* sid = reinterpret_cast<const int*>(base + 32 * W * 8);
+        m = sid[32 + idx];
+        s = sid[idx];
+        const int ns = 3 * m + 2;
+        sm = reinterpret_cast<double*>(row);
+        sm[0] = (double)(long long)row[0];
+        if (ACC != LSEFIT_ACCUM_F64) {
+            for (int k = 1; k < ns; ++k) {
+                const dflt v = bits_df(row[k]);
+                sm[k] = f32_to_f64_int(v.hi) + f32_to_f64_int(v.lo);
+            }
+        }
+        if (ACC == LSEFIT_ACCUM_F64) {
+            ok = load_map_f64(p, s, c, sc);
+        } else {
+            float cf, sf;
+            ok = load_map_f32(p, s, cf, sf);
+            c = f32_to_f64_int(cf);
+            sc = f32_to_f64_int(sf);
         }
     }
-    double c, sc;
-    bool ok;
-    if (ACC == LSEFIT_ACCUM_F64) {
-        ok = load_map_f64(p, s, c, sc);
-    } else {
-        float cf, sf;
-        ok = load_map_f32(p, s, cf, sf);
-        c = f32_to_f64_int(cf);
-        sc = f32_to_f64_int(sf);
-    }
+    // the solve is sized for the largest degree among the lanes solving together
+    // (FP64 instructions cost the same for 1 or 32 lanes; padding does not), and
+    // skips the un-map when every lane's map is the identity (c = 0, s = 1)
+    const int mw = (int)__reduce_max_sync(0xffffffffu, active ? (unsigned)m : 0u);
+    const bool id = __all_sync(0xffffffffu, !active || (__double_as_longlong(c) == 0ll &&
+                                                        __double_as_longlong(sc) == 0x3ff0000000000000ll));
+    if (!active) return;
     const int nc = p.m_max + 1;
-    const int st = solve_hankel_rt<NMAX>(m, sm, sm + 2 * m + 1, c, sc, ok, p.eps,
-                                         p.Xt ? p.Xt + s * nc : nullptr, p.X + s * nc, nc);
+    double* xt = p.Xt ? p.Xt + s * nc : nullptr;
+    double* x = p.X + s * nc;
+    const double* T = sm + 2 * m + 1;
+    int st;
+    switch (mw) {
+        case 1: st = solve_hankel_rt<1>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
+        case 2: st = solve_hankel_rt<2>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
+        case 3: st = solve_hankel_rt<3>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
+        case 4: st = solve_hankel_rt<4>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
+        default:
+            if constexpr (NMAX > 5) {
+                switch (mw) {
+                    case 5: st = solve_hankel_rt<5>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
+                    case 6: st = solve_hankel_rt<6>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
+                    case 7: st = solve_hankel_rt<7>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
+                    default: st = solve_hankel_rt<8>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
+                }
+            } else {
+                st = solve_hankel_rt<5>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id);
+            }
+            break;
+    }
     p.status[s] = st;
     if (p.sums) {
         const double qnan = __longlong_as_double(0x7ff8000000000000ll);
         const int stride = 3 * p.m_max + 2;
+        const int ns = 3 * m + 2;
         double* out = p.sums + s * stride;
         for (int k = 0; k < stride; ++k) out[k] = k < ns ? (ok ? sm[k] : qnan) : 0.0;
     }
@@ -462,14 +536,12 @@ template <int NMAX, int ACC>
 __device__ __forceinline__ void pend_solve(const BParams& p, Pend<NMAX>& q) {
     __syncwarp();
     const int lane = threadIdx.x & 31;
-    const int cnt = *q.count;
     unsigned char* base = reinterpret_cast<unsigned char*>(q.row);
     // the queue of warp w of this block is at pend_block + w * kWarpBytes; solve
     // entries relative to this warp's own queue
-    pend_solve_entry<NMAX, ACC>(p, base, 0, lane, lane < cnt);
+    pend_solve_entry<NMAX, ACC>(p, base, 0, lane, lane < q.n);
     __syncwarp();
-    if (lane == 0) *q.count = 0;
-    __syncwarp();
+    q.n = 0;
 }
 
 // Status and NaN row of a series that is not fitted at all (bad degree).
@@ -528,14 +600,14 @@ __device__ void block_task(const BParams& p, int t, int4 task, dflt* red, double
     const int slot_row = PendLayout<NMAX>::kStride;
     if (nch == 1) {
         if (tid == 0) {
-            const int slot = *q0.count;
+            const int slot = q0.n;
             unsigned long long* row = q0.row + slot * slot_row;
             row[0] = (unsigned long long)len;
             for (int a = 0; a < N; ++a) row[a + 1] = words[a];
             q0.sid[slot] = (int)s;
             q0.meta[slot] = M;
-            *q0.count = slot + 1;
         }
+        if (tid < 32) q0.n += 1;
     } else {
         const int stride = 3 * p.m_max + 1;
         if (tid < N) {
@@ -566,20 +638,20 @@ __device__ void block_task(const BParams& p, int t, int4 task, dflt* red, double
             }
             __syncthreads();
             if (tid == 0) {
-                const int slot = *q0.count;
+                const int slot = q0.n;
                 unsigned long long* row = q0.row + slot * slot_row;
                 row[0] = (unsigned long long)len;
                 for (int a = 0; a < N; ++a) row[a + 1] = reinterpret_cast<unsigned long long*>(comb)[a];
                 q0.sid[slot] = (int)s;
                 q0.meta[slot] = M;
-                *q0.count = slot + 1;
                 p.tickets[first] = 0u;
             }
+            if (tid < 32) q0.n += 1;
         }
     }
     if (tid < 32) {
         __syncwarp();
-        if (*q0.count == 32) pend_solve<NMAX, ACC>(p, q0);
+        if (q0.n == 32) pend_solve<NMAX, ACC>(p, q0);
     }
 }
 
@@ -697,7 +769,7 @@ __device__ void ring_task(const BParams& p, Ring& R, int& slot, int& pending, Cu
 #pragma unroll
         for (int a = 0; a < NP; ++a) v[a] = a < N ? A.acc[a] : 0.0;
         const double tot = warp_reduce_scatter_d<NP>(v);
-        const int qs = *q.count;
+        const int qs = q.n;
         unsigned long long* row = q.row + qs * PendLayout<NMAX>::kStride;
         if (lane < N) row[lane + 1] = (unsigned long long)__double_as_longlong(tot);
     } else {
@@ -737,19 +809,19 @@ __device__ void ring_task(const BParams& p, Ring& R, int& slot, int& pending, Cu
             }
         }
         const dflt tot = warp_reduce_scatter_df<NP>(v);
-        const int qs = *q.count;
+        const int qs = q.n;
         unsigned long long* row = q.row + qs * PendLayout<NMAX>::kStride;
         if (lane < N) row[lane + 1] = df_bits(tot);
     }
     if (lane == 0) {
-        const int qs = *q.count;
+        const int qs = q.n;
         q.row[qs * PendLayout<NMAX>::kStride] = (unsigned long long)count;
         q.sid[qs] = s;
         q.meta[qs] = M;
-        *q.count = qs + 1;
     }
+    q.n += 1;
     __syncwarp();
-    if (*q.count == 32) pend_solve<NMAX, ACC>(p, q);
+    if (q.n == 32) pend_solve<NMAX, ACC>(p, q);
 }
 
 template <int NMAX, int DT, int ACC>
@@ -805,15 +877,13 @@ __global__ void __launch_bounds__(kBBlock, 1) batched_kernel(BParams p) {
     int* counts = reinterpret_cast<int*>(comb + 32);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* pend_block = p.pend + (size_t)blockIdx.x * kBWarps * PendLayout<NMAX>::kWarpBytes;
+    // each warp's queue; block tasks queue their series in warp 0's (whose
+    // threads alone touch it there, so its count stays in warp 0's registers)
     Pend<NMAX> q;
-    q.bind(pend_block + warp * PendLayout<NMAX>::kWarpBytes, counts + warp);
-    Pend<NMAX> q0;
-    q0.bind(pend_block, counts);
-    if (lane == 0) *q.count = 0;
-    __syncthreads();
+    q.bind(pend_block + warp * PendLayout<NMAX>::kWarpBytes);
 
     // phase 1: block tasks
-    for (;;) {
+    for (; p.n_block_tasks > 0;) {
         if (tid == 0) s_task = (int)atomicAdd(&p.counters[0], 1u);
         __syncthreads();
         const int t = s_task;
@@ -825,7 +895,7 @@ __global__ void __launch_bounds__(kBBlock, 1) batched_kernel(BParams p) {
             if (tid == 0 && task.y == 0) mark_invalid(p, task.x);
             continue;
         }
-        dispatch_block<NMAX, DT, ACC>(p, t, task, m, red, blk, comb, q0, &s_last);
+        dispatch_block<NMAX, DT, ACC>(p, t, task, m, red, blk, comb, q, &s_last);
     }
     // phase 2: warp tasks through the warp's stage ring
     {
@@ -833,9 +903,6 @@ __global__ void __launch_bounds__(kBBlock, 1) batched_kernel(BParams p) {
         R.bind(smem + warp * kRingWarpBytes);
         Cursor cu;
         cursor_init(cu, p);
-        cursor_step(cu, p);     // index -> a
-        cursor_step(cu, p);     // a -> b
-        cursor_advance(cu, p);  // b -> current
         int pending = 0;
 #pragma unroll
         for (int k = 0; k < kRing; ++k)
@@ -847,6 +914,7 @@ __global__ void __launch_bounds__(kBBlock, 1) batched_kernel(BParams p) {
         }
     }
     // leftover queued series of all warps, solved 32 per warp across the block
+    if (lane == 0) counts[warp] = q.n;
     __syncthreads();
     {
         int total = 0;
@@ -858,6 +926,7 @@ __global__ void __launch_bounds__(kBBlock, 1) batched_kernel(BParams p) {
                 idx -= counts[ws];
                 ++ws;
             }
+            __syncwarp();  // the entry solve votes across the full warp
             pend_solve_entry<NMAX, ACC>(p, pend_block, ws, idx, g < total);
         }
     }

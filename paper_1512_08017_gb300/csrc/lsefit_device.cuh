@@ -679,9 +679,11 @@ __device__ __forceinline__ void unmap_padded(int m, const double* z, double c, d
     }
 }
 
+// identity: the caller knows c = 0 and s = 1 (the un-map is then the identity
+// exactly, and is skipped).
 template <int NMAX, bool CHOL = false>
 __device__ int solve_hankel_rt(int m, const double* S, const double* T, double c, double s,
-                               bool map_ok, double eps, double* Xt, double* X, int ncoef) {
+                               bool map_ok, double eps, double* Xt, double* X, int ncoef, bool identity = false) {
     constexpr int N = NMAX + 1;
     double z[N];
     int st = fit_precheck(m, S, T, map_ok);
@@ -696,7 +698,12 @@ __device__ int solve_hankel_rt(int m, const double* S, const double* T, double c
         return st;
     }
     double out[N];
-    unmap_padded<NMAX>(m, z, c, s, out);
+    if (identity) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) out[j] = z[j];
+    } else {
+        unmap_padded<NMAX>(m, z, c, s, out);
+    }
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         if (i < ncoef) {
