@@ -47,7 +47,7 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["lsefit", "reference"], default="lsefit")
     p.add_argument("--workload", default="single_large",
-                   choices=["single_large", "ragged_batch", "diff_batch", "single_fp64", "general"])
+                   choices=["single_large", "ragged_batch", "diff_batch", "single_fp64", "general", "solve"])
     p.add_argument("--kind", default="weighted", choices=["weighted", "chebyshev", "weighted_chebyshev"],
                    help="objective of the general workload")
     p.add_argument("--n", type=int, default=1 << 28, help="points of the single_large series")
@@ -465,6 +465,18 @@ def run_ragged_batch(args, dist: Dist):
         plain = {"value": N / (pms / 1e3), "unit": UNIT, "ms_per_step": pms, "host_wall_s": wall,
                  "launches_per_step": S, "desc": "one lsefit_fit launch per series from a host loop, no graph"}
 
+    # the residual/SSE pass over the same batch (reads x, y once more: 8 B/point),
+    # from a fit that also keeps the mapped-basis coefficients and the map
+    fwd_full = L.fit_batched(x, y, off, deg, iv, m_max=m_max, accum=args.accum, plan=plan)
+    res_out = L.residuals_batched(x, y, off, deg, fwd_full)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(res_out["sse"]).all())
+    rper, _ = _event_steps(lambda: L.residuals_batched(x, y, off, deg, fwd_full), args.steps, stream)
+    r_ms = dist.max(statistics.mean(rper))
+    residuals = {"ms_per_step": r_ms, "hbm_gbs": 8 * N / (r_ms / 1e3) / 1e9,
+                 "roofline": _roofline(8 * N, r_ms, "residuals_kernel<F32> (+ prep launch)", "residuals_f32"),
+                 "desc": "lsefit_residuals: SSE and V^T r per series from the fit's Xt and map"}
+
     e2e = None
     if not args.no_e2e:
         hX = torch.empty(S, m_max + 1, dtype=torch.float64).pin_memory()
@@ -512,6 +524,7 @@ def run_ragged_batch(args, dist: Dist):
         "roofline": _roofline(algo, step_ms, "batched_kernel<5,F32,comp> (+ prep launch)", "batched_f32_comp"),
         "plain_per_series": plain,
         "speedup_vs_plain": (plain["ms_per_step"] / (ms / args.steps)) if plain else None,
+        "residuals": residuals,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": 2 * args.steps,
     }
 
@@ -672,6 +685,66 @@ def run_diff_batch(args, dist: Dist):
         "speedup_vs_plain": (plain["ms_per_step"] / msb) if plain else None,
         "cpu_baseline": None, "e2e": e2e, "clocks": clk, "gpu_launches": 6 * args.steps,
     }
+
+
+# ---------------------------------------------------------------------------
+# solve: the normal equations of 65,536 degree-5 fits, by Gaussian elimination
+# and by Cholesky factorisation (one system per thread, FP64)
+# ---------------------------------------------------------------------------
+def run_solve(args, dist: Dist):
+    import torch
+    import synth
+    import paper_1512_08017_gb300 as L
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    m = 5
+    b = synth.ragged_batch(num_series=args.series, seed=synth.SEED_RAGGED + dist.rank)
+    S = len(b["degree"])
+    deg = np.full(S, m, dtype=np.int32)
+    x = torch.from_numpy(b["x"]).to(dev)
+    y = torch.from_numpy(b["y"]).to(dev)
+    fwd = L.fit_batched(x, y, b["offsets"], deg, b["interval"], m_max=m, accum="comp")
+    torch.cuda.synchronize()
+    sums, mp = fwd["sums"], fwd["map"]
+    ok = fwd["status"] == 0
+    stream = torch.cuda.current_stream()
+    res = {}
+    for method in ("gauss", "cholesky"):
+        X = torch.empty(S, m + 1, dtype=torch.float64, device=dev)
+        Xt = torch.empty_like(X)
+        st = torch.empty(S, dtype=torch.int32, device=dev)
+
+        def step():
+            L.solve(sums, m, map=mp, accum="comp", X=X, Xt=Xt, status=st, method=method)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        per, total = _event_steps(step, args.steps, stream)
+        res[method] = {"ms": dist.max(statistics.mean(per)), "Xt": Xt.clone(), "status": st.clone()}
+    both = ok & (res["gauss"]["status"] == 0) & (res["cholesky"]["status"] == 0)
+    a, c = res["gauss"]["Xt"][both], res["cholesky"]["Xt"][both]
+    agree = float(((a - c).norm(dim=1) / a.norm(dim=1)).max().item())
+    n1 = m + 1
+    flops = {"gauss": 2 * n1 ** 3 / 3 + 2 * n1 ** 2, "cholesky": n1 ** 3 / 3 + 2 * n1 ** 2}
+    out = {}
+    for k in res:
+        ms = res[k]["ms"]
+        out[k] = {"ms_per_launch": ms, "systems_per_s": S / (ms / 1e3),
+                  "gflops": S * flops[k] / (ms / 1e3) / 1e9,
+                  "singular": int((res[k]["status"] == 3).sum().item())}
+    ms_g = out["gauss"]["ms_per_launch"]
+    return {"metric": "normal-equation systems solved/s (degree 5, FP64 GE)", "value": out["gauss"]["systems_per_s"],
+            "unit": "systems/s", "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_g, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (power sums of the seeded ragged batch fitted at degree 5)",
+            "config": {"workload": f"{S} degree-5 normal-equation systems from one batched pass, "
+                                   "one system per thread", "series": S, "m": m},
+            "gauss": out["gauss"], "cholesky": out["cholesky"], "max_rel_diff_gauss_cholesky": agree,
+            "roofline": {"bound": "fp64 latency", "achieved": out["gauss"]["gflops"], "peak": 1250.0,
+                         "unit": "GFLOP/s", "frac": out["gauss"]["gflops"] / 1250.0, "traffic": None,
+                         "peak_source": "nominal FP64 (no measured FP64 figure)"},
+            "gpu_launches": 2 * args.steps}
 
 
 # ---------------------------------------------------------------------------
@@ -875,7 +948,8 @@ def main(argv=None):
     dist = Dist(args.gpus)
     try:
         runners = {"single_large": run_single_large, "ragged_batch": run_ragged_batch,
-                   "diff_batch": run_diff_batch, "single_fp64": run_single_fp64, "general": run_general}
+                   "diff_batch": run_diff_batch, "single_fp64": run_single_fp64, "general": run_general,
+                   "solve": run_solve}
         line = runners[args.workload](args, dist)
         if dist.rank == 0 and line is not None:
             print(json.dumps(line))

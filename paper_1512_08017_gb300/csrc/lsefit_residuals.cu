@@ -83,9 +83,15 @@ __device__ __forceinline__ float horner(const float* a, float t) {
     return v;
 }
 
+// FP32 arithmetic over [b, e): 16-byte vectors of x and y, kRsUnroll of each
+// in flight per thread (the scalar head and tail of a misaligned range load
+// point by point); compensated batch folded after every group of vectors.
+constexpr int kRsUnroll = 4;
+
 template <int DT, int M>
 __device__ __forceinline__ void rs_range_f32(const RsParams& p, int64_t s, int64_t b, int64_t e, int64_t rank,
                                              int64_t nthreads, RsAcc<M>& A) {
+    constexpr int ES = Elem<DT>::kSize, PV = Elem<DT>::kPerVec, U = kRsUnroll;
     const int nc = p.m_max + 1;
     float coef[M + 1];
 #pragma unroll
@@ -93,16 +99,71 @@ __device__ __forceinline__ void rs_range_f32(const RsParams& p, int64_t s, int64
     const float c = p.map ? (float)p.map[2 * s] : 0.0f;
     const float sc = p.map ? (float)p.map[2 * s + 1] : 1.0f;
     float* rout = static_cast<float*>(p.r);
-    int batch = 0;
-    for (int64_t i = b + rank; i < e; i += nthreads) {
+    int64_t head, nvec;
+    split_range<DT>(p.x, p.y, b, e, head, nvec);
+    // residuals go out as 16-byte vectors when the output array is 16-byte aligned
+    // (then every vector of points maps to PV/4 aligned float4 slots)
+    const bool rvec = rout != nullptr && (reinterpret_cast<uintptr_t>(rout) & 15) == 0;
+    const uint4* xv = reinterpret_cast<const uint4*>(static_cast<const char*>(p.x) + (b + head) * ES);
+    const uint4* yv = reinterpret_cast<const uint4*>(static_cast<const char*>(p.y) + (b + head) * ES);
+    auto feed = [&](uint4 xr, uint4 yr, int64_t i0) {
+        float xs[PV], ys[PV], rr[PV];
+        if (DT == LSEFIT_F32) {
+            xs[0] = __uint_as_float(xr.x); xs[1] = __uint_as_float(xr.y);
+            xs[2 % PV] = __uint_as_float(xr.z); xs[3 % PV] = __uint_as_float(xr.w);
+            ys[0] = __uint_as_float(yr.x); ys[1] = __uint_as_float(yr.y);
+            ys[2 % PV] = __uint_as_float(yr.z); ys[3 % PV] = __uint_as_float(yr.w);
+        } else {
+            const uint32_t xw[4] = {xr.x, xr.y, xr.z, xr.w};
+            const uint32_t yw[4] = {yr.x, yr.y, yr.z, yr.w};
+#pragma unroll
+            for (int k = 0; k < PV / 2; ++k) {
+                xs[2 * k] = bf16_lo(xw[k]); xs[2 * k + 1] = bf16_hi(xw[k]);
+                ys[2 * k] = bf16_lo(yw[k]); ys[2 * k + 1] = bf16_hi(yw[k]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PV; ++q) {
+            const float t = __fmul_rn(__fsub_rn(xs[q], c), sc);
+            rr[q] = __fsub_rn(ys[q], horner<M>(coef, t));
+            A.add(t, rr[q]);
+        }
+        if (rout) {
+            if (rvec) {
+#pragma unroll
+                for (int q = 0; q < PV; q += 4)
+                    *reinterpret_cast<float4*>(rout + i0 + q) = make_float4(rr[q], rr[q + 1], rr[q + 2], rr[q + 3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < PV; ++q) rout[i0 + q] = rr[q];
+            }
+        }
+    };
+    const int64_t vbase = b + head;
+    int64_t v = rank;
+    for (; v + (U - 1) * nthreads < nvec; v += U * nthreads) {
+        uint4 xr[U], yr[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            xr[u] = ld_stream16(xv + v + u * nthreads);
+            yr[u] = ld_stream16(yv + v + u * nthreads);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) feed(xr[u], yr[u], vbase + (v + u * nthreads) * PV);
+        A.fold();
+    }
+    for (; v < nvec; v += nthreads) {
+        feed(ld_stream16(xv + v), ld_stream16(yv + v), vbase + v * PV);
+        A.fold();
+    }
+    const int64_t tail0 = vbase + nvec * PV;
+    const int64_t nscalar = head + (e - tail0);
+    for (int64_t q = rank; q < nscalar; q += nthreads) {
+        const int64_t i = q < head ? b + q : tail0 + (q - head);
         const float t = __fmul_rn(__fsub_rn(Elem<DT>::ld(p.x, i), c), sc);
         const float r = __fsub_rn(Elem<DT>::ld(p.y, i), horner<M>(coef, t));
         if (rout) rout[i] = r;
         A.add(t, r);
-        if (++batch == 8) {
-            A.fold();
-            batch = 0;
-        }
     }
     A.fold();
 }

@@ -32,21 +32,22 @@ def _ref(xs, ys, m, lo, hi, fp32):
     return r, float(np.sum(res * res)), vtr, scale, res
 
 
-@pytest.mark.parametrize("dtype,accum", [(torch.float32, "comp"), (torch.float64, "f64")])
+@pytest.mark.parametrize("dtype,accum", [(torch.float32, "comp"), (torch.float64, "f64"),
+                                         (torch.bfloat16, "comp")])
 @pytest.mark.parametrize("tuning", [None, {"warp_max_len": 256, "chunk_len": 4096}])
 def test_residuals_against_oracle(L, dtype, accum, tuning):
     b = synth.ragged_batch(num_series=150, lmin=20, lmax=30000, seed=91)
-    xs = b["x"].astype(np.float64)
-    ys = b["y"].astype(np.float64)
     x = torch.from_numpy(b["x"]).to(dtype).cuda()
     y = torch.from_numpy(b["y"]).to(dtype).cuda()
+    xs = x.double().cpu().numpy()  # the stored values
+    ys = y.double().cpu().numpy()
     plan = L.BatchPlan(b["offsets"], 5, tuning=tuning, degree=b["degree"])
     fwd = L.fit_batched(x, y, b["offsets"], b["degree"], b["interval"], m_max=5, accum=accum, plan=plan)
     out = L.residuals_batched(x, y, b["offsets"], b["degree"], fwd, want_r=True)
     sse = out["sse"].cpu().numpy()
     vtr = out["vtr"].cpu().numpy()
     rr = out["r"].double().cpu().numpy()
-    tol = 1e-9 if dtype == torch.float64 else 1e-4
+    tol = 1e-9 if dtype == torch.float64 else (1e-4 if dtype == torch.float32 else 1e-3)
     checked = 0
     for s in range(150):
         lo, hi = int(b["offsets"][s]), int(b["offsets"][s + 1])
@@ -82,3 +83,21 @@ def test_table5_sum_of_squared_errors(L):
     assert abs(gpu_sse - oracle.sse(ref["X"], x, y)) <= 1e-8 * gpu_sse
     assert gpu_sse <= sse_f
     assert np.allclose(fwd["X"][0].cpu().numpy(), ref["X"], rtol=1e-8)
+
+
+def test_full_size_residuals_sampled(L):
+    """The 65,536-series batch at the benchmark's size: SSE of sampled series
+    against the oracle's residuals of its own fit."""
+    b = synth.ragged_batch()
+    x = torch.from_numpy(b["x"]).cuda()
+    y = torch.from_numpy(b["y"]).cuda()
+    fwd = L.fit_batched(x, y, b["offsets"], b["degree"], b["interval"], m_max=5, accum="comp")
+    out = L.residuals_batched(x, y, b["offsets"], b["degree"], fwd)
+    sse = out["sse"].cpu().numpy()
+    rng = np.random.default_rng(92)
+    for s in rng.choice(len(b["degree"]), 200, replace=False):
+        lo, hi = int(b["offsets"][s]), int(b["offsets"][s + 1])
+        xs = b["x"][lo:hi].astype(np.float64)
+        ys = b["y"][lo:hi].astype(np.float64)
+        _, sse_ref, _, _, _ = _ref(xs, ys, int(b["degree"][s]), *b["interval"][s], fp32=True)
+        assert abs(sse[s] - sse_ref) <= 1e-4 * sse_ref + 1e-30, (s, sse[s], sse_ref)
