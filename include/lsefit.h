@@ -305,7 +305,8 @@ typedef struct lsefit_tuning {
                                      or r*W + W-1-w on odd rounds; W warps in the grid);
                                  3 (0 = default) = one queue per degree class, longest
                                      first; every block starts on a class (blocks shared
-                                     out in proportion to the classes' points) and moves
+                                     out in proportion to the classes' points times a
+                                     per-degree cost per point) and moves
                                      to the next class with tasks left when its class runs
                                      dry, so the warps of an SM run the code of one degree.
                                  In 1 and 3 a warp's first three tasks of its first queue

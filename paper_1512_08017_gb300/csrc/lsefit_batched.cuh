@@ -219,9 +219,9 @@ struct Ring {
 // w task r*W + w, or r*W + W-1-w on odd rounds, W warps in the grid), or
 // from one queue per degree class (schedule 3): a block starts on the class
 // its index falls in when the blocks are shared out in proportion to the
-// classes' points (cls_block, set at launch), and a warp whose class has run
-// dry moves on to the next class with tasks left, so the warps of an SM keep
-// running the code of one degree.  In schedules 1 and 3 the first
+// classes' cost, points x cost per point of the degree (cls_block, set at
+// launch), and a warp whose class has run dry moves on to the next class with
+// tasks left, so the warps of an SM keep running the code of one degree.  In schedules 1 and 3 the first
 // kStaticRounds draws of a warp are fixed snake rounds over the warps of its
 // first queue and only later draws take an atomic ticket (offset past the
 // static rounds): a grid that starts with every warp hitting one counter

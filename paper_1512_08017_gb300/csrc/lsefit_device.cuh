@@ -647,35 +647,27 @@ __device__ __forceinline__ int fit_precheck(int m, const double* S, const double
     return fin ? LSEFIT_OK : LSEFIT_ERR_NONFINITE;
 }
 
-// Un-map of t-basis coefficients z (k <= m) to the monomials of x:
-// out_j = sum_{k>=j} z_k C(k,j) s^k (-c)^(k-j).
+// Un-map of t-basis coefficients z (k <= m) to the monomials of x, i.e. the
+// coefficients of f(x) = sum_k z_k (s (x - c))^k:  first r_k = z_k s^k (the
+// polynomial in u = x - c), then a Taylor shift by -c -- m passes of
+// synthetic division, r_j <- r_j - c r_{j+1} for j = m-1 down to i -- which
+// expands sum_k r_k (x - c)^k.  (m(m+1)/2 + 2m FP64 operations, where the
+// binomial expansion out_j = sum_{k>=j} z_k C(k,j) s^k (-c)^(k-j) takes about
+// 2(m+1)^2 + m(m+1)/2.)
 template <int NMAX>
 __device__ __forceinline__ void unmap_padded(int m, const double* z, double c, double s, double* out) {
     constexpr int N = NMAX + 1;
-    double binom[N];  // row k of Pascal's triangle
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        out[j] = 0.0;
-        binom[j] = 0.0;
-    }
-    binom[0] = 1.0;
     double sk = 1.0;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-        if (k > m) break;
-        if (k > 0) {
+        out[k] = (k <= m) ? z[k] * sk : 0.0;
+        if (k < m) sk *= s;
+    }
 #pragma unroll
-            for (int j = N - 1; j >= 1; --j) binom[j] += binom[j - 1];
-            sk *= s;
-        }
-        double cp = 1.0;  // (-c)^(k-j) as j runs from k down to 0
+    for (int i = 0; i < N - 1; ++i) {
 #pragma unroll
-        for (int j = N - 1; j >= 0; --j) {
-            if (j <= k) {
-                out[j] = fma(z[k] * binom[j] * sk, cp, out[j]);
-                cp *= -c;
-            }
-        }
+        for (int j = N - 2; j >= i; --j)
+            if (i < m && j < m) out[j] = fma(-c, out[j + 1], out[j]);
     }
 }
 

@@ -70,6 +70,17 @@ def check_batch(L, b, res, accum, stored_x=None, stored_y=None, series=None, fp3
         e = np.linalg.norm(Xt[s, : m + 1] - r["Xt"]) / np.linalg.norm(r["Xt"])
         assert e <= tol, (s, e, tol, m, hi - lo)
         assert np.all(X[s, m + 1:] == 0.0) and np.all(Xt[s, m + 1:] == 0.0)
+        if b.get("interval") is not None:
+            # the x-basis coefficients (the un-map of Xt) give the same polynomial: values
+            # across the interval agree up to the Xt tolerance plus the rounding of an
+            # x-basis evaluation (relative to the size of its terms)
+            xx = np.linspace(b["interval"][s][0], b["interval"][s][1], 5)
+            tt = r["s"] * (xx - r["c"])
+            pw = np.arange(m + 1)
+            f_ref = (r["Xt"][None, :] * tt[:, None] ** pw).sum(axis=1)
+            terms = X[s, : m + 1][None, :] * xx[:, None] ** pw
+            slack = 2 * tol * np.linalg.norm(r["Xt"]) * (m + 1) + 1e-11 * np.abs(terms).sum(axis=1)
+            assert np.all(np.abs(terms.sum(axis=1) - f_ref) <= slack), (s, m)
         # saved sums: S_0 exact, the rest close to the oracle's
         assert sums[s, 0] == hi - lo
         np.testing.assert_allclose(sums[s, 1: 2 * m + 1], r["S"][1:], rtol=1e-4, atol=1e-4 * (hi - lo))

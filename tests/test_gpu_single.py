@@ -289,3 +289,15 @@ def test_cholesky_statuses(L):
     sums, mp, _ = L.powersums(_dev(np.full(50, 2.0), f32), _dev(np.arange(50.0), f32), 2, "comp")
     X, Xt, st = L.solve(sums, 2, 2, mp, "comp", method="cholesky")
     assert L.status_names(st) == ["singular"] and torch.isnan(X).all()
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_fp64_mapped_coefficients(L, m):
+    """FP64 data on [0, 10] mapped to [-1, 1]: the un-mapped x-basis coefficients
+    match the oracle's (the un-map is well conditioned for c = 5, s = 0.2)."""
+    d = synth.single_fp64()
+    ref = oracle.fit_interval(d["x"], d["y"], m, 0.0, 10.0, fp32=False)
+    out = L.fit(_dev(d["x"]), _dev(d["y"]), m, accum="f64", interval=(0.0, 10.0))
+    assert L.status_names(out["status"]) == ["ok"]
+    assert _rel(out["Xt"].cpu().numpy(), ref["Xt"]) <= 1e-9
+    assert _rel(out["X"].cpu().numpy(), ref["X"]) <= 1e-9
