@@ -238,3 +238,15 @@ def test_full_size_weighted(L):
     del x, y, wd
     ref = oracle.fit_general_interval(d["x"], d["y"], 3, -1.0, 1.0, fp32=True, w=w)
     _check(L, out, ref, "comp", 3)
+
+
+def test_mapped_host_memory(L):
+    """Points and weights in pinned host memory are streamed by the kernel directly."""
+    n = (1 << 18) + 7
+    d = synth.small_series(n, seed=97, m=3)
+    w = synth.weights(n, seed=98)
+    x, y, wh = (torch.from_numpy(a).pin_memory() for a in (d["x"], d["y"], w))
+    out = L.fit_general(x, y, 3, w=wh, basis="chebyshev", accum="comp", interval=(-1.0, 1.0))
+    ref = oracle.fit_general_interval(d["x"].astype(np.float64), d["y"].astype(np.float64), 3, -1.0, 1.0,
+                                      fp32=True, w=w.astype(np.float64), basis="chebyshev")
+    _check(L, out, ref, "comp", 3)
