@@ -48,7 +48,7 @@ def parse_args(argv=None):
     p.add_argument("--impl", choices=["lsefit", "reference"], default="lsefit")
     p.add_argument("--workload", default="single_large",
                    choices=["single_large", "ragged_batch", "diff_batch", "single_fp64", "general", "solve"])
-    p.add_argument("--kind", default="weighted", choices=["weighted", "chebyshev", "weighted_chebyshev"],
+    p.add_argument("--kind", default="weighted", choices=["weighted", "chebyshev", "weighted_chebyshev", "chebyshev16"],
                    help="objective of the general workload")
     p.add_argument("--n", type=int, default=1 << 28, help="points of the single_large series")
     p.add_argument("--series", type=int, default=65536, help="series of the ragged_batch workload")
@@ -391,6 +391,15 @@ def _roofline(algo_bytes, kern_ms, kernel, key):
             "kernel_ms": kern_ms,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
             else "fallback 6800 GB/s"}
+
+
+def _roofline_fp64(flops, kern_ms, kernel):
+    """FP64-bound kernels: achieved GFLOP/s against the nominal FP64 rate (the
+    measured peaks cover HBM and bf16 only).  flops counts each FMA as two."""
+    achieved = flops / (kern_ms / 1e3) / 1e9
+    return {"bound": "fp64", "achieved": achieved, "peak": 1250.0, "unit": "GFLOP/s", "frac": achieved / 1250.0,
+            "traffic": None, "kernel": kernel, "kernel_ms": kern_ms,
+            "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 figure)"}
 
 
 # ---------------------------------------------------------------------------
@@ -809,10 +818,13 @@ GENERAL_KINDS = {
     "weighted_chebyshev": (True, "chebyshev", 8, (0.0, 1000.0),
                            "single series, n=2^28 FP32 points + FP32 weights (3 GiB), x ~ U[0,1000] mapped, "
                            "weighted Chebyshev basis, degrees 8..1 from one pass"),
+    "chebyshev16": (False, "chebyshev", 16, (0.0, 1000.0),
+                    "single series, n=2^28 FP32 points (2 GiB), x ~ U[0,1000] mapped to [-1,1], "
+                    "Chebyshev basis, degrees 16..1 from one pass (FP64 accumulation)"),
 }
 
 
-def cpu_baseline_general(x, y, w, m, basis, interval, target_s):
+def cpu_baseline_general(x, y, w, m, basis, interval, target_s, fp32=True):
     import oracle
     n = x.size
     sample = min(n, 1 << 22)
@@ -822,7 +834,7 @@ def cpu_baseline_general(x, y, w, m, basis, interval, target_s):
     reps, t_total = 0, 0.0
     while reps < 3 or t_total < target_s:
         t0 = time.perf_counter()
-        out = oracle.fit_general_interval(xs, ys, m, *interval, fp32=True, w=ws, basis=basis)
+        out = oracle.fit_general_interval(xs, ys, m, *interval, fp32=fp32, w=ws, basis=basis)
         t_total += time.perf_counter() - t0
         reps += 1
         if reps >= 1000:
@@ -840,6 +852,7 @@ def run_general(args, dist: Dist):
     import paper_1512_08017_gb300 as L
 
     weighted, basis, m, interval, desc = GENERAL_KINDS[args.kind]
+    accum = "f64" if m > 8 else args.accum  # degrees above 8: Chebyshev with FP64 accumulation
     dev = torch.device("cuda", torch.cuda.current_device())
     n = args.n
     hx = torch.empty(n, dtype=torch.float32).pin_memory()
@@ -857,10 +870,10 @@ def run_general(args, dist: Dist):
     x, y = hx.to(dev), hy.to(dev)
     w = hw.to(dev) if weighted else None
     stream = torch.cuda.current_stream()
-    out = L.fit_general(x, y, m, w=w, basis=basis, m_lo=1, accum=args.accum, interval=interval)
+    out = L.fit_general(x, y, m, w=w, basis=basis, m_lo=1, accum=accum, interval=interval)
 
     def step():
-        L.fit_general(x, y, m, w=w, basis=basis, m_lo=1, accum=args.accum, interval=interval, out=out)
+        L.fit_general(x, y, m, w=w, basis=basis, m_lo=1, accum=accum, interval=interval, out=out)
 
     for _ in range(args.warmup):
         step()
@@ -900,7 +913,7 @@ def run_general(args, dist: Dist):
         copy_mode = {"value": dist.world * n * e_steps / (e_ms / 1e3), "ms_per_step": e_ms / e_steps}
 
         def e2e_mapped():
-            L.fit_general(hx, hy, m, w=hw, basis=basis, m_lo=1, accum=args.accum, interval=interval, out=out)
+            L.fit_general(hx, hy, m, w=hw, basis=basis, m_lo=1, accum=accum, interval=interval, out=out)
             hX.copy_(out["X"][m - 1], non_blocking=True)
 
         for _ in range(2):
@@ -915,20 +928,23 @@ def run_general(args, dist: Dist):
                "h2d_bytes_per_step": streams * n * 4, "d2h_bytes_per_step": (m + 1) * 8,
                "steps": e_steps, "ms_per_step": best["ms_per_step"],
                "mode": "mapped" if best is mapped_mode else "copy", "copy": copy_mode, "mapped": mapped_mode}
-    kname = "gen_kernel_f32<{},F32,{},W={},CHEB={}>".format(m, args.accum, int(weighted), int(basis == "chebyshev"))
+    kname = "gen_kernel_{}<{},F32,{},W={},CHEB={}>".format("f64" if accum == "f64" else "f32", m, accum,
+                                                          int(weighted), int(basis == "chebyshev"))
     cpu = None
     if dist.rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline_general(d["x"] if (lo, hi) == (-1.0, 1.0) else hx.numpy(), d["y"],
-                                   hw.numpy() if weighted else None, m, basis, interval, args.cpu_seconds)
+                                   hw.numpy() if weighted else None, m, basis, interval, args.cpu_seconds,
+                                   fp32=accum != "f64")
     return {
         "metric": METRIC, "value": dist.world * n * args.steps / (ms_max / 1e3), "unit": UNIT,
         "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded)",
         "config": {"workload": desc, "n": n, "m": list(range(m, 0, -1)), "basis": basis, "weighted": weighted,
-                   "accum": args.accum, "l2": "inputs larger than L2; no flush",
+                   "accum": accum, "l2": "inputs larger than L2; no flush",
                    "parallelism": f"replicas x{dist.world}"},
-        "roofline": _roofline(algo_bytes, kern_ms, kname, f"general_{args.kind}"),
+        "roofline": _roofline(algo_bytes, kern_ms, kname, f"general_{args.kind}") if accum != "f64" else
+        _roofline_fp64(n * (8 * m + 2 + (3 if weighted else 0)), kern_ms, kname),
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": args.steps,
     }
 

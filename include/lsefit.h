@@ -55,6 +55,8 @@ extern "C" {
 typedef struct CUstream_st* lsefit_stream_t;
 
 #define LSEFIT_MAX_DEGREE 8
+/* Highest degree of lsefit_fit_general in the Chebyshev basis with FP64 accumulation. */
+#define LSEFIT_MAX_DEGREE_CHEBYSHEV 16
 #define LSEFIT_ABI_VERSION 1
 
 /* Return and status codes. */
@@ -249,7 +251,12 @@ size_t lsefit_fit_general_workspace_size(int m);
  *  n, dtype, m, m_lo, accum, interval
  *             as lsefit_fit (degrees m_lo..m from the one pass; the map
  *             t = s (x - c) of [lo, hi] onto [-1, 1] or t = x without an
- *             interval).  dtype F64 requires accum F64.
+ *             interval).  dtype F64 requires accum F64.  m <= LSEFIT_MAX_DEGREE,
+ *             or, in the Chebyshev basis with accum F64 (whose normal matrix
+ *             stays well conditioned where the monomial one does not),
+ *             m <= LSEFIT_MAX_DEGREE_CHEBYSHEV; a Chebyshev degree above
+ *             LSEFIT_MAX_DEGREE with FP32 accumulation is
+ *             LSEFIT_ERR_UNSUPPORTED.
  *  basis      LSEFIT_BASIS_MONOMIAL or LSEFIT_BASIS_CHEBYSHEV.
  *  X          device double[(m - m_lo + 1)][m + 1]: monomial coefficients of x
  *             (row d - m_lo for degree d, entries beyond d zero; NaN rows for

@@ -8,8 +8,8 @@
 using namespace lsefit;
 
 extern "C" size_t lsefit_fit_general_workspace_size(int m) {
-    if (m < 1 || m > LSEFIT_MAX_DEGREE) return 0;
-    const size_t fit_ws = lsefit_powersums_workspace_size(m);
+    if (m < 1 || m > LSEFIT_MAX_DEGREE_CHEBYSHEV) return 0;
+    const size_t fit_ws = m <= LSEFIT_MAX_DEGREE ? lsefit_powersums_workspace_size(m) : 0;
     const size_t gen_ws = kAlign + align_up((size_t)kMaxGrid * (3 * m + 2) * sizeof(double), kAlign);
     return gen_ws > fit_ws ? gen_ws : fit_ws;
 }
@@ -18,9 +18,10 @@ extern "C" int lsefit_fit_general(const void* x, const void* y, const void* w, i
                                   int m_lo, int accum, int basis, const double* interval, double* X, double* Xb,
                                   double* sums, double* map, int32_t* status, void* workspace,
                                   size_t workspace_bytes, lsefit_stream_t stream) {
-    if (m < 1 || m > LSEFIT_MAX_DEGREE || n < 0 || m_lo < 1 || m_lo > m) return LSEFIT_ERR_INVALID_ARG;
-    if (X == nullptr || status == nullptr) return LSEFIT_ERR_INVALID_ARG;
     if (basis != LSEFIT_BASIS_MONOMIAL && basis != LSEFIT_BASIS_CHEBYSHEV) return LSEFIT_ERR_INVALID_ARG;
+    const int mmax = basis == LSEFIT_BASIS_CHEBYSHEV ? LSEFIT_MAX_DEGREE_CHEBYSHEV : LSEFIT_MAX_DEGREE;
+    if (m < 1 || m > mmax || n < 0 || m_lo < 1 || m_lo > m) return LSEFIT_ERR_INVALID_ARG;
+    if (X == nullptr || status == nullptr) return LSEFIT_ERR_INVALID_ARG;
     if (dtype < LSEFIT_F64 || dtype > LSEFIT_BF16) return LSEFIT_ERR_INVALID_ARG;
     if (accum < LSEFIT_ACCUM_NAIVE || accum > LSEFIT_ACCUM_F64) return LSEFIT_ERR_INVALID_ARG;
     if (dtype == LSEFIT_F64 && accum != LSEFIT_ACCUM_F64) return LSEFIT_ERR_UNSUPPORTED;
@@ -36,8 +37,12 @@ extern "C" int lsefit_fit_general(const void* x, const void* y, const void* w, i
         if (w != nullptr && resolve_device_pointer(w) != LSEFIT_OK) return LSEFIT_ERR_INVALID_ARG;
     }
     const bool cheb = basis == LSEFIT_BASIS_CHEBYSHEV;
-    gen_kernel_t k = w != nullptr ? (cheb ? gen_pick_weighted_chebyshev(m, dtype, accum) : gen_pick_weighted(m, dtype, accum))
-                                  : gen_pick_chebyshev(m, dtype, accum);
+    gen_kernel_t k;
+    if (m > LSEFIT_MAX_DEGREE)  // Chebyshev only (checked above)
+        k = w != nullptr ? gen_pick_weighted_chebyshev_high(m, dtype, accum) : gen_pick_chebyshev_high(m, dtype, accum);
+    else
+        k = w != nullptr ? (cheb ? gen_pick_weighted_chebyshev(m, dtype, accum) : gen_pick_weighted(m, dtype, accum))
+                         : gen_pick_chebyshev(m, dtype, accum);
     if (k == nullptr) return LSEFIT_ERR_UNSUPPORTED;
     GenParams p;
     p.x = x;

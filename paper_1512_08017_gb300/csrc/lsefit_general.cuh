@@ -498,9 +498,36 @@ gen_kernel_t gen_pick(int m, int dtype, int accum) {
     }
 }
 
-// One translation unit per kind instantiates its kernels.
+// Chebyshev degrees 9..16 (FP64 accumulation only: the compensated FP32 form
+// of 3m+2 = 50 slots would need about 300 registers per thread).
+template <int M, bool W>
+gen_kernel_t gen_pick_high_m(int dtype, int accum) {
+    if (accum != LSEFIT_ACCUM_F64) return nullptr;
+    if (dtype == LSEFIT_F64) return gen_kernel_f64<M, LSEFIT_F64, W, true, 2>;
+    if (dtype == LSEFIT_F32) return gen_kernel_f64<M, LSEFIT_F32, W, true, 2>;
+    return gen_kernel_f64<M, LSEFIT_BF16, W, true, 1>;
+}
+
+template <bool W>
+gen_kernel_t gen_pick_high(int m, int dtype, int accum) {
+    switch (m) {
+        case 9: return gen_pick_high_m<9, W>(dtype, accum);
+        case 10: return gen_pick_high_m<10, W>(dtype, accum);
+        case 11: return gen_pick_high_m<11, W>(dtype, accum);
+        case 12: return gen_pick_high_m<12, W>(dtype, accum);
+        case 13: return gen_pick_high_m<13, W>(dtype, accum);
+        case 14: return gen_pick_high_m<14, W>(dtype, accum);
+        case 15: return gen_pick_high_m<15, W>(dtype, accum);
+        case 16: return gen_pick_high_m<16, W>(dtype, accum);
+        default: return nullptr;
+    }
+}
+
+// One translation unit per kind (and per degree range) instantiates its kernels.
 gen_kernel_t gen_pick_weighted(int m, int dtype, int accum);
 gen_kernel_t gen_pick_chebyshev(int m, int dtype, int accum);
 gen_kernel_t gen_pick_weighted_chebyshev(int m, int dtype, int accum);
+gen_kernel_t gen_pick_chebyshev_high(int m, int dtype, int accum);
+gen_kernel_t gen_pick_weighted_chebyshev_high(int m, int dtype, int accum);
 
 }  // namespace lsefit

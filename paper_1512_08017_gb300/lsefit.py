@@ -37,6 +37,7 @@ ERR_SCRATCH_LIMIT = 9
 F64, F32, BF16 = 0, 1, 2
 ACCUM = {"naive": 0, "comp": 1, "f64": 2}
 MAX_DEGREE = 8
+MAX_DEGREE_CHEBYSHEV = 16  # Chebyshev basis with FP64 accumulation
 
 # per-fit status names (same vocabulary as the oracle's)
 STATUS_NAMES = {OK: "ok", ERR_N_TOO_SMALL: "n_too_small", ERR_SINGULAR: "singular",
@@ -320,8 +321,9 @@ def fit_general(x: torch.Tensor, y: torch.Tensor, m: int, w: torch.Tensor | None
     if basis not in BASES:
         raise ValueError(f"basis must be one of {sorted(BASES)}")
     m_lo = m if m_lo is None else m_lo
-    if not (1 <= m_lo <= m <= MAX_DEGREE):
-        raise ValueError(f"need 1 <= m_lo <= m <= {MAX_DEGREE}")
+    mmax = MAX_DEGREE_CHEBYSHEV if basis == "chebyshev" else MAX_DEGREE
+    if not (1 <= m_lo <= m <= mmax):
+        raise ValueError(f"need 1 <= m_lo <= m <= {mmax}")
     dev = _device_of(x)
     sh = _stream_handle(stream)
     iv = _interval_tensor(interval, dev)

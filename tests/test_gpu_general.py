@@ -250,3 +250,36 @@ def test_mapped_host_memory(L):
     ref = oracle.fit_general_interval(d["x"].astype(np.float64), d["y"].astype(np.float64), 3, -1.0, 1.0,
                                       fp32=True, w=w.astype(np.float64), basis="chebyshev")
     _check(L, out, ref, "comp", 3)
+
+
+@pytest.mark.parametrize("m", [9, 12, 16])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_chebyshev_high_degrees(L, m, weighted):
+    """Degrees above 8 in the Chebyshev basis with FP64 accumulation (x on
+    [0, 1000] mapped): the normal matrix stays well conditioned where the
+    monomial one is singular at the FP64 threshold."""
+    d = synth.precision(n=1 << 20, m=m)
+    lo, hi = d["interval"]
+    w = synth.weights(1 << 20, seed=99) if weighted else None
+    x, y = _dev(d["x"]), _dev(d["y"])
+    wd = _dev(w) if weighted else None
+    xs, ys = _stored(x), _stored(y)
+    ref = oracle.fit_general_interval(xs, ys, m, lo, hi, fp32=False, w=_stored(wd) if weighted else None,
+                                      basis="chebyshev")
+    assert np.linalg.cond(ref["G"]) < 1e3
+    out = L.fit_general(x, y, m, w=wd, basis="chebyshev", m_lo=m - 2, accum="f64", interval=(lo, hi))
+    _check(L, out, ref, "f64", m, row=2)
+    # the same degree in the monomial basis: a normal matrix orders of magnitude worse
+    # conditioned (singular at the FP64 threshold from about m = 12)
+    mono = oracle.fit_general_interval(xs, ys, m, lo, hi, fp32=False, basis="monomial")
+    assert mono["status"] == "singular" or np.linalg.cond(mono["G"]) > 1e3 * np.linalg.cond(ref["G"])
+
+
+def test_chebyshev_high_degree_limits(L):
+    x = _dev(np.linspace(-1, 1, 1000))
+    with pytest.raises(L.LsefitError):  # FP32 accumulation is limited to degree 8
+        L.fit_general(x, x, 9, basis="chebyshev", accum="comp")
+    with pytest.raises(ValueError):
+        L.fit_general(x, x, 9, basis="monomial", accum="f64")
+    with pytest.raises(ValueError):
+        L.fit_general(x, x, 17, basis="chebyshev", accum="f64")

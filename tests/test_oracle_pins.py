@@ -480,7 +480,7 @@ def test_integer_weights_are_repeated_points(basis):
     assert _rel(r["X"], ref["X"]) <= 1e3 * cond * EPS
 
 
-@pytest.mark.parametrize("m", [2, 4, 8])
+@pytest.mark.parametrize("m", [2, 4, 8, 12, 16])
 def test_chebyshev_against_chebfit(m):
     """Chebyshev coefficients of the (weighted) fit equal numpy's chebfit, an
     independent least-squares solve of the Chebyshev-Vandermonde system."""
