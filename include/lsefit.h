@@ -57,7 +57,7 @@ typedef struct CUstream_st* lsefit_stream_t;
 #define LSEFIT_MAX_DEGREE 8
 /* Highest degree of lsefit_fit_general in the Chebyshev basis with FP64 accumulation. */
 #define LSEFIT_MAX_DEGREE_CHEBYSHEV 16
-#define LSEFIT_ABI_VERSION 1
+#define LSEFIT_ABI_VERSION 2
 
 /* Return and status codes. */
 enum {

@@ -36,6 +36,7 @@ ERR_SCRATCH_LIMIT = 9
 
 F64, F32, BF16 = 0, 1, 2
 ACCUM = {"naive": 0, "comp": 1, "f64": 2}
+ABI_VERSION = 2  # LSEFIT_ABI_VERSION the structures below are laid out for
 MAX_DEGREE = 8
 MAX_DEGREE_CHEBYSHEV = 16  # Chebyshev basis with FP64 accumulation
 
@@ -124,6 +125,9 @@ def _load():
 
 
 lib = _load()
+if lib.lsefit_abi_version() != ABI_VERSION:
+    raise ImportError(f"liblsefit.so reports ABI version {lib.lsefit_abi_version()}, this binding expects "
+                      f"{ABI_VERSION}: rebuild it (python -c 'import __graft_entry__ as g; g.build()')")
 
 
 def status_string(code: int) -> str:
