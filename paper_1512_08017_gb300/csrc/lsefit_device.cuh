@@ -774,17 +774,23 @@ __device__ __forceinline__ void accumulate_range(AccF32<M, COMP, SHL>& A, const 
     const uint4* xv = reinterpret_cast<const uint4*>(static_cast<const char*>(x) + (b + head) * ES);
     const uint4* yv = reinterpret_cast<const uint4*>(static_cast<const char*>(y) + (b + head) * ES);
     int64_t v = rank;
-    for (; v + (UNROLL - 1) * nthreads < nvec; v += UNROLL * nthreads) {
-        uint4 xr[UNROLL], yr[UNROLL];
+    // groups of UNROLL vectors per compensated batch: two at high degree, where
+    // the fold of 3m+1 slots is a large share of the per-point work
+    constexpr int G = (UNROLL == 2 && M >= 7) ? 2 : 1;
+    for (; v + (G * UNROLL - 1) * nthreads < nvec; v += G * UNROLL * nthreads) {
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
-            xr[u] = ld_stream16(xv + v + u * nthreads);
-            yr[u] = ld_stream16(yv + v + u * nthreads);
-        }
+        for (int gi = 0; gi < G; ++gi) {
+            uint4 xr[UNROLL], yr[UNROLL];
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
-            if (u == 0) feed_vec<M, DT, COMP, MAP, COMP, SHL>(A, xr[u], yr[u], c2, s2);
-            else feed_vec<M, DT, COMP, MAP, false, SHL>(A, xr[u], yr[u], c2, s2);
+            for (int u = 0; u < UNROLL; ++u) {
+                xr[u] = ld_stream16(xv + v + (gi * UNROLL + u) * nthreads);
+                yr[u] = ld_stream16(yv + v + (gi * UNROLL + u) * nthreads);
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                if (gi == 0 && u == 0) feed_vec<M, DT, COMP, MAP, COMP, SHL>(A, xr[u], yr[u], c2, s2);
+                else feed_vec<M, DT, COMP, MAP, false, SHL>(A, xr[u], yr[u], c2, s2);
+            }
         }
         A.fold();
     }

@@ -197,16 +197,23 @@ __device__ __forceinline__ void accumulate_range_gen(AccGenF32<M, COMP, W, CHEB>
         }
     };
     int64_t v = rank;
-    for (; v + (UNROLL - 1) * nthreads < nvec; v += UNROLL * nthreads) {
-        uint4 xr[UNROLL], yr[UNROLL], wr[UNROLL];
+    // groups of UNROLL vectors per compensated batch: two at high degree, where
+    // the fold of 3m+2 slots is a large share of the per-point work
+    constexpr int G = (UNROLL == 2 && M >= 7) ? 2 : 1;
+    for (; v + (G * UNROLL - 1) * nthreads < nvec; v += G * UNROLL * nthreads) {
 #pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
-            xr[u] = ld_stream16(xv + v + u * nthreads);
-            yr[u] = ld_stream16(yv + v + u * nthreads);
-            wr[u] = W ? ld_stream16(wv + v + u * nthreads) : make_uint4(0, 0, 0, 0);
+        for (int gi = 0; gi < G; ++gi) {
+            uint4 xr[UNROLL], yr[UNROLL], wr[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                const int64_t o = v + (gi * UNROLL + u) * nthreads;
+                xr[u] = ld_stream16(xv + o);
+                yr[u] = ld_stream16(yv + o);
+                wr[u] = W ? ld_stream16(wv + o) : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) feed(xr[u], yr[u], wr[u], gi == 0 && u == 0);
         }
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u) feed(xr[u], yr[u], wr[u], u == 0);
         A.fold();
     }
     for (; v < nvec; v += nthreads) {
