@@ -56,6 +56,8 @@ def parse_args(argv=None):
     p.add_argument("--tuning", default=None,
                    help="batched schedule as JSON (e.g. '{\"warp_max_len\": 1048576}'); default: autotune")
     p.add_argument("--accum", default="comp", choices=["comp", "naive", "f64"])
+    p.add_argument("--basis", default="monomial", choices=["monomial", "chebyshev"],
+                   help="basis of the ragged_batch fit (chebyshev: no residual pass or plain comparison)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0,
@@ -437,7 +439,7 @@ def run_ragged_batch(args, dist: Dist):
     stream = torch.cuda.current_stream()
 
     def fwd():
-        L.fit_batched(x, y, off, deg, iv, m_max=m_max, accum=args.accum, plan=plan, out=out)
+        L.fit_batched(x, y, off, deg, iv, m_max=m_max, accum=args.accum, plan=plan, out=out, basis=args.basis)
 
     g = _graph(fwd, stream)
     for _ in range(args.warmup):
@@ -458,7 +460,7 @@ def run_ragged_batch(args, dist: Dist):
 
     # plain per-series path: one single-series fit launch per series from a host loop
     plain = None
-    if not args.no_plain:
+    if not args.no_plain and args.basis == "monomial":
         wsz = L.lib.lsefit_powersums_workspace_size(m_max)
         ws = torch.zeros(wsz, dtype=torch.uint8, device=dev)
         Xp = torch.empty(S, m_max + 1, dtype=torch.float64, device=dev)
@@ -495,15 +497,17 @@ def run_ragged_batch(args, dist: Dist):
 
     # the residual/SSE pass over the same batch (reads x, y once more: 8 B/point),
     # from a fit that also keeps the mapped-basis coefficients and the map
-    fwd_full = L.fit_batched(x, y, off, deg, iv, m_max=m_max, accum=args.accum, plan=plan)
-    res_out = L.residuals_batched(x, y, off, deg, fwd_full)
-    torch.cuda.synchronize()
-    assert bool(torch.isfinite(res_out["sse"]).all())
-    rper, _ = _event_steps(lambda: L.residuals_batched(x, y, off, deg, fwd_full), args.steps, stream)
-    r_ms = dist.max(statistics.mean(rper))
-    residuals = {"ms_per_step": r_ms, "hbm_gbs": 8 * N / (r_ms / 1e3) / 1e9,
-                 "roofline": _roofline(8 * N, r_ms, "residuals_kernel<F32> (+ prep launch)", "residuals_f32"),
-                 "desc": "lsefit_residuals: SSE and V^T r per series from the fit's Xt and map"}
+    residuals = None
+    if args.basis == "monomial":
+        fwd_full = L.fit_batched(x, y, off, deg, iv, m_max=m_max, accum=args.accum, plan=plan)
+        res_out = L.residuals_batched(x, y, off, deg, fwd_full)
+        torch.cuda.synchronize()
+        assert bool(torch.isfinite(res_out["sse"]).all())
+        rper, _ = _event_steps(lambda: L.residuals_batched(x, y, off, deg, fwd_full), args.steps, stream)
+        r_ms = dist.max(statistics.mean(rper))
+        residuals = {"ms_per_step": r_ms, "hbm_gbs": 8 * N / (r_ms / 1e3) / 1e9,
+                     "roofline": _roofline(8 * N, r_ms, "residuals_kernel<F32> (+ prep launch)", "residuals_f32"),
+                     "desc": "lsefit_residuals: SSE and V^T r per series from the fit's Xt and map"}
 
     e2e = None
     if not args.no_e2e:
@@ -545,11 +549,14 @@ def run_ragged_batch(args, dist: Dist):
         "data": "synthetic (seeded ragged batch)",
         "config": {"workload": f"batched ragged: {S} series, lengths log-uniform 16..65536, degrees 1..5, "
                                "per-series intervals; one persistent launch in a CUDA graph",
-                   "series": S, "points": N, "accum": args.accum, "tuning": tuning,
+                   "series": S, "points": N, "accum": args.accum, "basis": args.basis, "tuning": tuning,
                    "autotune_s": t_tune, "plan_build_s": t_plan, "autotune_candidates": len(tried),
                    "l2": f"inputs ({8 * N / 1e9:.1f} GB) larger than L2; no flush"},
         "hbm_gbs": algo / (step_ms / 1e3) / 1e9,
-        "roofline": _roofline(algo, step_ms, "batched_kernel<5,F32,comp> (+ prep launch)", "batched_f32_comp"),
+        "roofline": _roofline(algo, step_ms,
+                              "batched_kernel<5,F32,{}{}> (+ prep launch)".format(
+                                  args.accum, ",chebyshev" if args.basis != "monomial" else ""),
+                              "batched_f32_comp" if args.basis == "monomial" else "batched_f32_comp_chebyshev"),
         "plain_per_series": plain,
         "speedup_vs_plain": (plain["ms_per_step"] / (ms / args.steps)) if plain else None,
         "residuals": residuals,

@@ -292,7 +292,9 @@ typedef struct lsefit_batch {
     int32_t m_max;            /* row stride of X/Xt is m_max+1, of sums 3*m_max+2 */
     int32_t dtype;            /* LSEFIT_F32 / LSEFIT_BF16 / LSEFIT_F64 */
     int32_t accum;            /* LSEFIT_ACCUM_* */
-    int32_t reserved;
+    int32_t basis;            /* LSEFIT_BASIS_MONOMIAL (0, the paper's fit) or LSEFIT_BASIS_CHEBYSHEV:
+                                 the basis of t the fit is computed in (see lsefit_fit_general);
+                                 Chebyshev needs accum COMP or F64 (F32/BF16 storage) or F64 */
 } lsefit_batch;
 
 /* Tuning of the batched schedule (0 in a field = library default). */
@@ -384,10 +386,12 @@ size_t lsefit_batched_workspace_size(const lsefit_plan* plan);
  *  plan      host, from lsefit_plan_build for this layout, with device task arrays.
  *  X         device double[num_series][m_max+1]; row s holds degree[s]+1
  *            coefficients, the rest of the row is zero.
- *  Xt        device, same shape, or NULL.
+ *  Xt        device, same shape, or NULL: the coefficients in the basis of t
+ *            (t^k, or T_k(t) when batch->basis is LSEFIT_BASIS_CHEBYSHEV).
  *  sums      device double[num_series][3*m_max+2] or NULL: S_0..S_2d, T_0..T_d
  *            of degree d = degree[s] at the start of the row (needed by
- *            lsefit_backward), rest zero.
+ *            lsefit_backward), rest zero; in the Chebyshev basis the moments
+ *            sum T_p(t) and sum T_j(t) y.
  *  map       device double[num_series][2] or NULL: {c, s} used per series.
  *  status    device int32[num_series]: per-series status.
  *  workspace device, >= lsefit_batched_workspace_size(plan), 256-byte aligned;
@@ -431,7 +435,8 @@ size_t lsefit_residuals_workspace_size(const lsefit_plan* plan);
  * solution (the normal equations of Section II), so it measures how well a
  * fit satisfies them.  FP32 per point, compensated double-float sums, FP64
  * chunk combine; FP64 throughout for FP64 data.
- *  batch     as for lsefit_fit_batched (interval unused: the map is `map`).
+ *  batch     as for lsefit_fit_batched (interval unused: the map is `map`);
+ *            basis must be LSEFIT_BASIS_MONOMIAL (else LSEFIT_ERR_UNSUPPORTED).
  *  plan      the layout's plan, device task arrays set.
  *  Xt        device double[num_series][m_max+1] (from lsefit_fit_batched).
  *  map       device double[num_series][2] {c, s} or NULL (identity).
@@ -464,7 +469,8 @@ size_t lsefit_backward_workspace_size(const lsefit_plan* plan);
  *   with f(t) = sum_k Xt_k t^k; powers are recomputed, not stored.
  * Two launches: the lambda solves (one series per thread), then a second
  * pass over the points with the forward plan's tasks.
- *  batch     as for lsefit_fit_batched (same layout and degrees).
+ *  batch     as for lsefit_fit_batched (same layout and degrees); basis must
+ *            be LSEFIT_BASIS_MONOMIAL (else LSEFIT_ERR_UNSUPPORTED).
  *  plan      the forward's plan (same layout), device task arrays set.
  *  sums      device double[num_series][3*m_max+2] from lsefit_fit_batched.
  *  Xt        device double[num_series][m_max+1] from lsefit_fit_batched.

@@ -384,6 +384,7 @@ extern "C" int lsefit_backward(const lsefit_batch* batch, const lsefit_plan* pla
         b.m_max > LSEFIT_MAX_DEGREE)
         return LSEFIT_ERR_INVALID_ARG;
     if (b.dtype < LSEFIT_F64 || b.dtype > LSEFIT_BF16) return LSEFIT_ERR_INVALID_ARG;
+    if (b.basis != LSEFIT_BASIS_MONOMIAL) return LSEFIT_ERR_UNSUPPORTED;  // evaluates t^k polynomials
     if (b.accum < LSEFIT_ACCUM_NAIVE || b.accum > LSEFIT_ACCUM_F64) return LSEFIT_ERR_INVALID_ARG;
     if (b.num_series == 0) return LSEFIT_OK;
     if (sums == nullptr || Xt == nullptr || gX == nullptr || b.offsets == nullptr || b.degree == nullptr)

@@ -12,7 +12,13 @@
 
 namespace lsefit {
 
-static batched_kernel_t pick_batched(int dtype, int accum, int nmax) {
+static batched_kernel_t pick_batched(int dtype, int accum, int nmax, int basis) {
+    if (basis == LSEFIT_BASIS_CHEBYSHEV) {
+        if (dtype == LSEFIT_F64) return batched_f64_f64_cheb(nmax);
+        if (accum == LSEFIT_ACCUM_COMP) return dtype == LSEFIT_F32 ? batched_f32_comp_cheb(nmax) : batched_bf16_comp_cheb(nmax);
+        if (accum == LSEFIT_ACCUM_F64 && dtype == LSEFIT_F32) return batched_f32_f64_cheb(nmax);
+        return nullptr;
+    }
     if (dtype == LSEFIT_F64) return batched_f64_f64(nmax);
     if (dtype == LSEFIT_F32) {
         if (accum == LSEFIT_ACCUM_NAIVE) return batched_f32_naive(nmax);
@@ -175,6 +181,7 @@ extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* 
         b.accum > LSEFIT_ACCUM_F64)
         return LSEFIT_ERR_INVALID_ARG;
     if (b.dtype == LSEFIT_F64 && b.accum != LSEFIT_ACCUM_F64) return LSEFIT_ERR_UNSUPPORTED;
+    if (b.basis != LSEFIT_BASIS_MONOMIAL && b.basis != LSEFIT_BASIS_CHEBYSHEV) return LSEFIT_ERR_INVALID_ARG;
     if (b.num_series == 0) return LSEFIT_OK;
     if (b.offsets == nullptr || b.degree == nullptr) return LSEFIT_ERR_INVALID_ARG;
     if (plan->total_points > 0 && (b.x == nullptr || b.y == nullptr)) return LSEFIT_ERR_INVALID_ARG;
@@ -214,7 +221,8 @@ extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* 
     p.pend = reinterpret_cast<unsigned char*>(ws + ws_pend_off(plan));
 
     const int nmax = b.m_max <= 5 ? 5 : 8;
-    batched_kernel_t k = pick_batched(b.dtype, b.accum, nmax);
+    batched_kernel_t k = pick_batched(b.dtype, b.accum, nmax, b.basis);
+    if (k == nullptr) return LSEFIT_ERR_UNSUPPORTED;
     const size_t smem = batched_smem_bytes(nmax);
     static std::mutex mu;
     static std::vector<std::pair<int, const void*>> configured;

@@ -458,7 +458,7 @@ __device__ __forceinline__ void ring_wait(int pending) {
 // Solve one queued series (entry idx of warp ws's queue in this block), if
 // `active`.  Called by all 32 lanes of a warp together (the degree and map
 // votes below span the full warp).  Converts the entry's sums to FP64 in place.
-template <int NMAX, int ACC>
+template <int NMAX, int ACC, bool CHEB = false>
 __device__ __noinline__ void pend_solve_entry(const BParams& p, unsigned char* pend_block, int ws, int idx,
                                               bool active) {
     constexpr int W = PendLayout<NMAX>::kStride;
@@ -503,6 +503,27 @@ __device__ __noinline__ void pend_solve_entry(const BParams& p, unsigned char* p
     double* x = p.X + s * nc;
     const double* T = sm + 2 * m + 1;
     int st;
+    if (CHEB) {
+        // Chebyshev basis: G from the moments (sm[0] = n), Xt holds the Chebyshev coefficients
+        switch (mw) {
+            case 1: st = solve_general_rt<1, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc); break;
+            case 2: st = solve_general_rt<2, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc); break;
+            case 3: st = solve_general_rt<3, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc); break;
+            case 4: st = solve_general_rt<4, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc); break;
+            default:
+                if constexpr (NMAX > 5) {
+                    switch (mw) {
+                        case 5: st = solve_general_rt<5, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc); break;
+                        case 6: st = solve_general_rt<6, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc); break;
+                        case 7: st = solve_general_rt<7, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc); break;
+                        default: st = solve_general_rt<8, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc); break;
+                    }
+                } else {
+                    st = solve_general_rt<5, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc);
+                }
+                break;
+        }
+    } else
     switch (mw) {
         case 1: st = solve_hankel_rt<1>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
         case 2: st = solve_hankel_rt<2>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
@@ -532,14 +553,14 @@ __device__ __noinline__ void pend_solve_entry(const BParams& p, unsigned char* p
 }
 
 // The warp solves its full queue (32 series), one per lane, and empties it.
-template <int NMAX, int ACC>
+template <int NMAX, int ACC, bool CHEB = false>
 __device__ __forceinline__ void pend_solve(const BParams& p, Pend<NMAX>& q) {
     __syncwarp();
     const int lane = threadIdx.x & 31;
     unsigned char* base = reinterpret_cast<unsigned char*>(q.row);
     // the queue of warp w of this block is at pend_block + w * kWarpBytes; solve
     // entries relative to this warp's own queue
-    pend_solve_entry<NMAX, ACC>(p, base, 0, lane, lane < q.n);
+    pend_solve_entry<NMAX, ACC, CHEB>(p, base, 0, lane, lane < q.n);
     __syncwarp();
     q.n = 0;
 }
@@ -566,7 +587,7 @@ struct Unroll {
 // ---------------------------------------------------------------------------
 // One block task: chunk `chunk` of `nch` of series s.
 // ---------------------------------------------------------------------------
-template <int NMAX, int DT, int ACC, int M>
+template <int NMAX, int DT, int ACC, int M, bool CHEB = false>
 __device__ void block_task(const BParams& p, int t, int4 task, dflt* red, double* blk, double* comb,
                            Pend<NMAX>& q0, int* s_last) {
     constexpr int N = 3 * M + 1;
@@ -582,17 +603,17 @@ __device__ void block_task(const BParams& p, int t, int4 task, dflt* red, double
     if constexpr (ACC == LSEFIT_ACCUM_F64) {
         double c, sc;
         const bool ok = load_map_f64(p, s, c, sc);
-        AccF64<M> A;
+        AccF64<M, CHEB> A;
         A.init();
-        if (ok) accumulate_range_f64<M, DT, kBlockUnroll, true>(A, p.x, p.y, b, e, tid, kBBlock, c, sc);
+        if (ok) accumulate_range_f64<M, DT, kBlockUnroll, true, CHEB>(A, p.x, p.y, b, e, tid, kBBlock, c, sc);
         block_reduce_d<kBBlock, N>([&](int a) { return A.acc[a]; }, reinterpret_cast<double*>(red), blk);
         // blk[a] (doubles) == words[a]
     } else {
         float c, sc;
         const bool ok = load_map_f32(p, s, c, sc);
-        AccF32<M, ACC == LSEFIT_ACCUM_COMP, true> A;
+        AccF32<M, ACC == LSEFIT_ACCUM_COMP, true, CHEB> A;
         A.init();
-        if (ok) accumulate_range<M, DT, ACC == LSEFIT_ACCUM_COMP, true, kBlockUnroll, true>(
+        if (ok) accumulate_range<M, DT, ACC == LSEFIT_ACCUM_COMP, true, kBlockUnroll, true, CHEB>(
             A, p.x, p.y, b, e, tid, kBBlock, c, sc);
         block_reduce_df2<kBBlock, N>([&](int a) { return A.result(a); }, red, reinterpret_cast<dflt*>(blk));
     }
@@ -651,7 +672,7 @@ __device__ void block_task(const BParams& p, int t, int4 task, dflt* red, double
     }
     if (tid < 32) {
         __syncwarp();
-        if (q0.n == 32) pend_solve<NMAX, ACC>(p, q0);
+        if (q0.n == 32) pend_solve<NMAX, ACC, CHEB>(p, q0);
     }
 }
 
@@ -663,21 +684,22 @@ __device__ void block_task(const BParams& p, int t, int4 task, dflt* red, double
 // Zero the pair (t, y) where its element index e (first of the pair) is
 // outside [lo, hi): a zero abscissa and ordinate add nothing to the sums of
 // degree >= 1 (S_0 is the count, kept apart).
-__device__ __forceinline__ void mask_pair(u64& t, u64& y, int e, int lo, int hi) {
+__device__ __forceinline__ void mask_pair(u64& t, u64& y, u64& seed, int e, int lo, int hi) {
     float t0, t1, y0, y1;
     up2(t, t0, t1);
     up2(y, y0, y1);
     const bool ok0 = e >= lo && e < hi, ok1 = e + 1 >= lo && e + 1 < hi;
     t = pk2(ok0 ? t0 : 0.0f, ok1 ? t1 : 0.0f);
     y = pk2(ok0 ? y0 : 0.0f, ok1 ? y1 : 0.0f);
+    seed = pk2(ok0 ? 1.0f : 0.0f, ok1 ? 1.0f : 0.0f);
 }
 
 // Accumulate the points [lo, hi) of one landed stage (element indices
 // relative to the stage's first vector).  Full vectors and the partial first
 // and last vectors of a series take the same packed code; a partial vector
 // only masks its pairs.
-template <int M, int DT, bool COMP, bool SHL>
-__device__ __forceinline__ void stage_accumulate_f32(AccF32<M, COMP, SHL>& A, const unsigned char* xb,
+template <int M, int DT, bool COMP, bool SHL, bool CHEB = false>
+__device__ __forceinline__ void stage_accumulate_f32(AccF32<M, COMP, SHL, CHEB>& A, const unsigned char* xb,
                                                      const unsigned char* yb, long long r0, int n, float cf,
                                                      float sf) {
     constexpr int PV = Elem<DT>::kPerVec, P = kStageBytes / Elem<DT>::kSize;
@@ -708,14 +730,15 @@ __device__ __forceinline__ void stage_accumulate_f32(AccF32<M, COMP, SHL>& A, co
                 yp = pk2(bf16_lo(yw[k]), bf16_hi(yw[k]));
             }
             tp = mul2(sub2(tp, c2), s2);
-            if (part) mask_pair(tp, yp, v * PV + 2 * k, lo, hi);
-            A.template add_pair<false>(tp, yp);
+            u64 seed = CHEB ? pk2(1.0f, 1.0f) : 0ull;
+            if (part) mask_pair(tp, yp, seed, v * PV + 2 * k, lo, hi);
+            A.template add_pair<false>(tp, yp, seed);
         }
     }
 }
 
-template <int M, int DT>
-__device__ __forceinline__ void stage_accumulate_f64(AccF64<M>& A, const unsigned char* xb,
+template <int M, int DT, bool CHEB = false>
+__device__ __forceinline__ void stage_accumulate_f64(AccF64<M, CHEB>& A, const unsigned char* xb,
                                                      const unsigned char* yb, long long r0, int n, double c,
                                                      double sc) {
     constexpr int PV = Elem<DT>::kPerVec;
@@ -740,7 +763,7 @@ __device__ __forceinline__ void stage_accumulate_f64(AccF64<M>& A, const unsigne
 
 // One series streamed through the ring.  On entry the stage at `slot` is its
 // first stage and has landed; on return `slot` is the stage after its last.
-template <int NMAX, int DT, int ACC, int M>
+template <int NMAX, int DT, int ACC, int M, bool CHEB = false>
 __device__ void ring_task(const BParams& p, Ring& R, int& slot, int& pending, Cursor& cu, Pend<NMAX>& q) {
     constexpr int N = 3 * M + 1;
     constexpr int NP = N <= 16 ? 16 : 32;
@@ -751,12 +774,12 @@ __device__ void ring_task(const BParams& p, Ring& R, int& slot, int& pending, Cu
     if constexpr (ACC == LSEFIT_ACCUM_F64) {
         const bool ok = !isnan(mraw.x);
         const double c = ok ? mraw.x : 0.0, sc = ok ? mraw.y : 1.0;
-        AccF64<M> A;
+        AccF64<M, CHEB> A;
         A.init();
         for (;;) {
             const long long r0 = R.rec[slot].r0;
             const int n = R.rec[slot].n, flags = R.rec[slot].flags;
-            if (ok) stage_accumulate_f64<M, DT>(A, R.x + slot * kStageBytes, R.y + slot * kStageBytes, r0, n, c, sc);
+            if (ok) stage_accumulate_f64<M, DT, CHEB>(A, R.x + slot * kStageBytes, R.y + slot * kStageBytes, r0, n, c, sc);
             count += n;
             __syncwarp();
             --pending;
@@ -776,14 +799,14 @@ __device__ void ring_task(const BParams& p, Ring& R, int& slot, int& pending, Cu
         const float2 mf = *reinterpret_cast<const float2*>(&mraw);
         const bool ok = !isnan(mf.x);
         const float c = ok ? mf.x : 0.0f, sc = ok ? mf.y : 1.0f;
-        AccF32<M, ACC == LSEFIT_ACCUM_COMP, true> A;
+        AccF32<M, ACC == LSEFIT_ACCUM_COMP, true, CHEB> A;
         A.init();
         int since_fold = 0;
         for (;;) {
             const long long r0 = R.rec[slot].r0;
             const int n = R.rec[slot].n, flags = R.rec[slot].flags;
             if (ok)
-                stage_accumulate_f32<M, DT, ACC == LSEFIT_ACCUM_COMP, true>(A, R.x + slot * kStageBytes,
+                stage_accumulate_f32<M, DT, ACC == LSEFIT_ACCUM_COMP, true, CHEB>(A, R.x + slot * kStageBytes,
                                                                             R.y + slot * kStageBytes, r0, n, c, sc);
             if (++since_fold == kFoldStages) {
                 A.fold_reset();
@@ -821,52 +844,52 @@ __device__ void ring_task(const BParams& p, Ring& R, int& slot, int& pending, Cu
     }
     q.n += 1;
     __syncwarp();
-    if (q.n == 32) pend_solve<NMAX, ACC>(p, q);
+    if (q.n == 32) pend_solve<NMAX, ACC, CHEB>(p, q);
 }
 
-template <int NMAX, int DT, int ACC>
+template <int NMAX, int DT, int ACC, bool CHEB = false>
 __device__ __forceinline__ void dispatch_ring(const BParams& p, int m, Ring& R, int& slot, int& pending,
                                               Cursor& cu, Pend<NMAX>& q) {
     switch (m) {
-        case 1: ring_task<NMAX, DT, ACC, 1>(p, R, slot, pending, cu, q); break;
-        case 2: ring_task<NMAX, DT, ACC, 2>(p, R, slot, pending, cu, q); break;
-        case 3: ring_task<NMAX, DT, ACC, 3>(p, R, slot, pending, cu, q); break;
-        case 4: ring_task<NMAX, DT, ACC, 4>(p, R, slot, pending, cu, q); break;
-        case 5: ring_task<NMAX, DT, ACC, 5>(p, R, slot, pending, cu, q); break;
+        case 1: ring_task<NMAX, DT, ACC, 1, CHEB>(p, R, slot, pending, cu, q); break;
+        case 2: ring_task<NMAX, DT, ACC, 2, CHEB>(p, R, slot, pending, cu, q); break;
+        case 3: ring_task<NMAX, DT, ACC, 3, CHEB>(p, R, slot, pending, cu, q); break;
+        case 4: ring_task<NMAX, DT, ACC, 4, CHEB>(p, R, slot, pending, cu, q); break;
+        case 5: ring_task<NMAX, DT, ACC, 5, CHEB>(p, R, slot, pending, cu, q); break;
         default:
             if constexpr (NMAX > 5) {
                 switch (m) {
-                    case 6: ring_task<NMAX, DT, ACC, 6>(p, R, slot, pending, cu, q); break;
-                    case 7: ring_task<NMAX, DT, ACC, 7>(p, R, slot, pending, cu, q); break;
-                    default: ring_task<NMAX, DT, ACC, 8>(p, R, slot, pending, cu, q); break;
+                    case 6: ring_task<NMAX, DT, ACC, 6, CHEB>(p, R, slot, pending, cu, q); break;
+                    case 7: ring_task<NMAX, DT, ACC, 7, CHEB>(p, R, slot, pending, cu, q); break;
+                    default: ring_task<NMAX, DT, ACC, 8, CHEB>(p, R, slot, pending, cu, q); break;
                 }
             }
             break;
     }
 }
 
-template <int NMAX, int DT, int ACC>
+template <int NMAX, int DT, int ACC, bool CHEB = false>
 __device__ __forceinline__ void dispatch_block(const BParams& p, int t, int4 task, int m, dflt* red,
                                                double* blk, double* comb, Pend<NMAX>& q0, int* s_last) {
     switch (m) {
-        case 1: block_task<NMAX, DT, ACC, 1>(p, t, task, red, blk, comb, q0, s_last); break;
-        case 2: block_task<NMAX, DT, ACC, 2>(p, t, task, red, blk, comb, q0, s_last); break;
-        case 3: block_task<NMAX, DT, ACC, 3>(p, t, task, red, blk, comb, q0, s_last); break;
-        case 4: block_task<NMAX, DT, ACC, 4>(p, t, task, red, blk, comb, q0, s_last); break;
-        case 5: block_task<NMAX, DT, ACC, 5>(p, t, task, red, blk, comb, q0, s_last); break;
+        case 1: block_task<NMAX, DT, ACC, 1, CHEB>(p, t, task, red, blk, comb, q0, s_last); break;
+        case 2: block_task<NMAX, DT, ACC, 2, CHEB>(p, t, task, red, blk, comb, q0, s_last); break;
+        case 3: block_task<NMAX, DT, ACC, 3, CHEB>(p, t, task, red, blk, comb, q0, s_last); break;
+        case 4: block_task<NMAX, DT, ACC, 4, CHEB>(p, t, task, red, blk, comb, q0, s_last); break;
+        case 5: block_task<NMAX, DT, ACC, 5, CHEB>(p, t, task, red, blk, comb, q0, s_last); break;
         default:
             if constexpr (NMAX > 5) {
                 switch (m) {
-                    case 6: block_task<NMAX, DT, ACC, 6>(p, t, task, red, blk, comb, q0, s_last); break;
-                    case 7: block_task<NMAX, DT, ACC, 7>(p, t, task, red, blk, comb, q0, s_last); break;
-                    default: block_task<NMAX, DT, ACC, 8>(p, t, task, red, blk, comb, q0, s_last); break;
+                    case 6: block_task<NMAX, DT, ACC, 6, CHEB>(p, t, task, red, blk, comb, q0, s_last); break;
+                    case 7: block_task<NMAX, DT, ACC, 7, CHEB>(p, t, task, red, blk, comb, q0, s_last); break;
+                    default: block_task<NMAX, DT, ACC, 8, CHEB>(p, t, task, red, blk, comb, q0, s_last); break;
                 }
             }
             break;
     }
 }
 
-template <int NMAX, int DT, int ACC>
+template <int NMAX, int DT, int ACC, bool CHEB = false>
 __global__ void __launch_bounds__(kBBlock, 1) batched_kernel(BParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_task;
@@ -895,7 +918,7 @@ __global__ void __launch_bounds__(kBBlock, 1) batched_kernel(BParams p) {
             if (tid == 0 && task.y == 0) mark_invalid(p, task.x);
             continue;
         }
-        dispatch_block<NMAX, DT, ACC>(p, t, task, m, red, blk, comb, q, &s_last);
+        dispatch_block<NMAX, DT, ACC, CHEB>(p, t, task, m, red, blk, comb, q, &s_last);
     }
     // phase 2: warp tasks through the warp's stage ring
     {
@@ -910,7 +933,7 @@ __global__ void __launch_bounds__(kBBlock, 1) batched_kernel(BParams p) {
         int slot = 0;
         while (pending > 0) {
             ring_wait(pending);
-            dispatch_ring<NMAX, DT, ACC>(p, R.rec[slot].deg, R, slot, pending, cu, q);
+            dispatch_ring<NMAX, DT, ACC, CHEB>(p, R.rec[slot].deg, R, slot, pending, cu, q);
         }
     }
     // leftover queued series of all warps, solved 32 per warp across the block
@@ -927,7 +950,7 @@ __global__ void __launch_bounds__(kBBlock, 1) batched_kernel(BParams p) {
                 ++ws;
             }
             __syncwarp();  // the entry solve votes across the full warp
-            pend_solve_entry<NMAX, ACC>(p, pend_block, ws, idx, g < total);
+            pend_solve_entry<NMAX, ACC, CHEB>(p, pend_block, ws, idx, g < total);
         }
     }
     __syncthreads();
@@ -949,6 +972,12 @@ typedef void (*batched_kernel_t)(BParams);
         return nmax <= 5 ? batched_kernel<5, DT, ACC> : batched_kernel<8, DT, ACC>; \
     }
 
+// The Chebyshev-basis kernels (compensated FP32 and FP64 accumulation).
+#define LSEFIT_BATCHED_INSTANTIATE_CHEB(NAME, DT, ACC)                                         \
+    batched_kernel_t NAME(int nmax) {                                                         \
+        return nmax <= 5 ? batched_kernel<5, DT, ACC, true> : batched_kernel<8, DT, ACC, true>; \
+    }
+
 batched_kernel_t batched_f32_naive(int nmax);
 batched_kernel_t batched_f32_comp(int nmax);
 batched_kernel_t batched_f32_f64(int nmax);
@@ -956,5 +985,9 @@ batched_kernel_t batched_bf16_naive(int nmax);
 batched_kernel_t batched_bf16_comp(int nmax);
 batched_kernel_t batched_bf16_f64(int nmax);
 batched_kernel_t batched_f64_f64(int nmax);
+batched_kernel_t batched_f32_comp_cheb(int nmax);
+batched_kernel_t batched_bf16_comp_cheb(int nmax);
+batched_kernel_t batched_f32_f64_cheb(int nmax);
+batched_kernel_t batched_f64_f64_cheb(int nmax);
 
 }  // namespace lsefit

@@ -222,7 +222,10 @@ struct Nacc {
 //  * SHL = true: (hi, lo) are scalars; the two lanes of the batch sum are
 //    added first (one rounding of the batch's own size), then added to hi
 //    exactly (4 registers per accumulator; 8 scalar instructions).
-template <int M, bool COMP, bool SHL = false>
+// CHEB: the basis values are the Chebyshev polynomials T_k(t) (recurrence
+// T_{k+1} = 2t T_k - T_{k-1}) instead of the powers t^k; the slots keep the
+// same layout (moments of degree 1..2M, then the right-hand sides).
+template <int M, bool COMP, bool SHL = false, bool CHEB = false>
 struct AccF32 {
     static constexpr int N = 3 * M + 1;
     u64 acc[N];
@@ -249,10 +252,14 @@ struct AccF32 {
     }
 
     // Add the two points (t.x, y.x), (t.y, y.y).  FIRST assigns instead of
-    // adding (the first pair of a compensated batch).
+    // adding (the first pair of a compensated batch).  seed: 1 per valid lane,
+    // 0 for an empty lane (read only by the Chebyshev recurrence, whose
+    // T_0 = 1 would otherwise make an empty lane with t = 0 count in T_2).
     template <bool FIRST>
-    __device__ __forceinline__ void add_pair(u64 t, u64 y) {
+    __device__ __forceinline__ void add_pair(u64 t, u64 y, u64 seed = 0ull) {
         u64 p = t;
+        u64 pm1 = seed;       // T_{k-2} (Chebyshev)
+        const u64 t2 = CHEB ? add2(t, t) : 0ull;
         if (FIRST) {
             acc[2 * M] = y;
             acc[0] = p;
@@ -264,7 +271,13 @@ struct AccF32 {
         }
 #pragma unroll
         for (int k = 2; k <= 2 * M; ++k) {
-            p = mul2(p, t);
+            if (CHEB) {
+                const u64 pk = fma2(t2, p, pm1 ^ 0x8000000080000000ull);
+                pm1 = p;
+                p = pk;
+            } else {
+                p = mul2(p, t);
+            }
             if (FIRST) {
                 acc[k - 1] = p;
                 if (k <= M) acc[2 * M + k] = mul2(p, y);
@@ -329,8 +342,8 @@ struct AccF32 {
     }
 };
 
-// FP64 accumulator.
-template <int M>
+// FP64 accumulator (CHEB: Chebyshev basis values, as AccF32).
+template <int M, bool CHEB = false>
 struct AccF64 {
     static constexpr int N = 3 * M + 1;
     double acc[N];
@@ -339,13 +352,19 @@ struct AccF64 {
         for (int a = 0; a < N; ++a) acc[a] = 0.0;
     }
     __device__ __forceinline__ void add_point(double t, double y) {
-        double p = t;
+        double p = t, pm1 = 1.0;
         acc[2 * M] += y;
         acc[0] += p;
         acc[2 * M + 1] = fma(p, y, acc[2 * M + 1]);
 #pragma unroll
         for (int k = 2; k <= 2 * M; ++k) {
-            p *= t;
+            if (CHEB) {
+                const double pk = fma(t + t, p, -pm1);
+                pm1 = p;
+                p = pk;
+            } else {
+                p *= t;
+            }
             acc[k - 1] += p;
             if (k <= M) acc[2 * M + k] = fma(p, y, acc[2 * M + k]);
         }
@@ -710,6 +729,99 @@ __device__ int solve_hankel_rt(int m, const double* S, const double* T, double c
     return LSEFIT_OK;
 }
 
+// Monomial coefficients of sum_k a_k T_k(t) (k <= m): the recurrence of the
+// basis applied to coefficient rows, P_{k+1}(t) = 2 t P_k(t) - P_{k-1}(t).
+template <int NMAX>
+__device__ __forceinline__ void cheb_to_mono(int m, const double* a, double* out) {
+    constexpr int N = NMAX + 1;
+    double pm1[N], p[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        pm1[j] = j == 0 ? 1.0 : 0.0;
+        p[j] = j == 1 ? 1.0 : 0.0;
+        out[j] = a[0] * pm1[j] + (m >= 1 ? a[1] * p[j] : 0.0);
+    }
+#pragma unroll
+    for (int k = 2; k < N; ++k) {
+        if (k > m) break;
+#pragma unroll
+        for (int j = N - 1; j >= 0; --j) {
+            const double nj = (j > 0 ? 2.0 * p[j - 1] : 0.0) - pm1[j];
+            pm1[j] = p[j];
+            p[j] = nj;
+            out[j] = fma(a[k], nj, out[j]);
+        }
+    }
+}
+
+// Solve of the generalised normal equations from the moments Mo[0..2m] and
+// right-hand sides T[0..m] (count = number of points).  Monomial basis:
+// G[j][k] = Mo[j+k]; Chebyshev: G[j][k] = (Mo[j+k] + Mo[|j-k|]) / 2.
+// Singular when a pivot is at or below (m+1) * eps * max|G|.  Writes Xb (the
+// coefficients in the basis of t) and X (monomials of x), NaN on failure.
+template <int NMAX, bool CHEB>
+__device__ int solve_general_rt(int m, const double* Mo, const double* T, double count, double c, double s,
+                                bool map_ok, double eps, double* Xb, double* X, int ncoef) {
+    constexpr int N = NMAX + 1;
+    int st = LSEFIT_OK;
+    if (!map_ok) st = LSEFIT_ERR_BAD_INTERVAL;
+    else if (!(count >= (double)(m + 1))) st = LSEFIT_ERR_N_TOO_SMALL;
+    if (st == LSEFIT_OK) {
+        bool fin = true;
+        for (int k = 0; k <= 2 * m; ++k) fin = fin && isfinite(Mo[k]);
+        for (int k = 0; k <= m; ++k) fin = fin && isfinite(T[k]);
+        if (!fin) st = LSEFIT_ERR_NONFINITE;
+    }
+    double z[N];
+    if (st == LSEFIT_OK) {
+        double A[N][N + 1];
+        double amax = 0.0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                double g = (j == k) ? 1.0 : 0.0;
+                if (j <= m && k <= m) {
+                    g = CHEB ? 0.5 * (Mo[j + k] + Mo[j > k ? j - k : k - j]) : Mo[j + k];
+                    amax = fmax(amax, fabs(g));
+                }
+                A[j][k] = g;
+            }
+            A[j][N] = (j <= m) ? T[j] : 0.0;
+        }
+        st = ge_padded<NMAX>(m, A, (double)(m + 1) * eps * amax, z);
+    }
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    if (st != LSEFIT_OK) {
+        for (int i = 0; i < ncoef; ++i) {
+            const double v = i <= m ? qnan : 0.0;
+            if (Xb) Xb[i] = v;
+            X[i] = v;
+        }
+        return st;
+    }
+    double zt[N], out[N];
+    if (CHEB) {
+        cheb_to_mono<NMAX>(m, z, zt);
+    } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j) zt[j] = z[j];
+    }
+    unmap_padded<NMAX>(m, zt, c, s, out);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (i < ncoef) {
+            if (Xb) Xb[i] = i <= m ? z[i] : 0.0;
+            X[i] = i <= m ? out[i] : 0.0;
+        }
+    }
+    for (int i = N; i < ncoef; ++i) {
+        if (Xb) Xb[i] = 0.0;
+        X[i] = 0.0;
+    }
+    return LSEFIT_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Accumulation of the points of one contiguous range [b, e) by `nthreads`
 // cooperating threads (`rank` = this thread's index among them): 16-byte
@@ -734,8 +846,9 @@ __device__ __forceinline__ void split_range(const void* x, const void* y, int64_
 }
 
 // Unpack one 16-byte vector of x and of y into packed pairs and feed them.
-template <int M, int DT, bool COMP, bool MAP, bool FIRST, bool SHL = false>
-__device__ __forceinline__ void feed_vec(AccF32<M, COMP, SHL>& A, uint4 xv, uint4 yv, u64 c2, u64 s2) {
+template <int M, int DT, bool COMP, bool MAP, bool FIRST, bool SHL = false, bool CHEB = false>
+__device__ __forceinline__ void feed_vec(AccF32<M, COMP, SHL, CHEB>& A, uint4 xv, uint4 yv, u64 c2, u64 s2) {
+    const u64 one2 = CHEB ? pk2(1.0f, 1.0f) : 0ull;
     if (DT == LSEFIT_F32) {
         u64 xa = pk2(__uint_as_float(xv.x), __uint_as_float(xv.y));
         u64 xb = pk2(__uint_as_float(xv.z), __uint_as_float(xv.w));
@@ -745,8 +858,8 @@ __device__ __forceinline__ void feed_vec(AccF32<M, COMP, SHL>& A, uint4 xv, uint
             xa = mul2(sub2(xa, c2), s2);
             xb = mul2(sub2(xb, c2), s2);
         }
-        A.template add_pair<FIRST>(xa, ya);
-        A.template add_pair<false>(xb, yb);
+        A.template add_pair<FIRST>(xa, ya, one2);
+        A.template add_pair<false>(xb, yb, one2);
     } else {  // BF16: 8 points per vector
         const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
         const uint32_t yw[4] = {yv.x, yv.y, yv.z, yv.w};
@@ -755,16 +868,16 @@ __device__ __forceinline__ void feed_vec(AccF32<M, COMP, SHL>& A, uint4 xv, uint
             u64 xp = pk2(bf16_lo(xw[q]), bf16_hi(xw[q]));
             u64 yp = pk2(bf16_lo(yw[q]), bf16_hi(yw[q]));
             if (MAP) xp = mul2(sub2(xp, c2), s2);
-            if (q == 0) A.template add_pair<FIRST>(xp, yp);
-            else A.template add_pair<false>(xp, yp);
+            if (q == 0) A.template add_pair<FIRST>(xp, yp, one2);
+            else A.template add_pair<false>(xp, yp, one2);
         }
     }
 }
 
 // FP32/BF16 storage, FP32 arithmetic.  In compensated mode each thread's
 // batch (UNROLL vectors, or one scalar point) is folded into its TwoSum pairs.
-template <int M, int DT, bool COMP, bool MAP, int UNROLL, bool SHL = false>
-__device__ __forceinline__ void accumulate_range(AccF32<M, COMP, SHL>& A, const void* x, const void* y,
+template <int M, int DT, bool COMP, bool MAP, int UNROLL, bool SHL = false, bool CHEB = false>
+__device__ __forceinline__ void accumulate_range(AccF32<M, COMP, SHL, CHEB>& A, const void* x, const void* y,
                                                  int64_t b, int64_t e, int64_t rank, int64_t nthreads,
                                                  float cf, float sf) {
     constexpr int ES = Elem<DT>::kSize, PV = Elem<DT>::kPerVec;
@@ -788,14 +901,14 @@ __device__ __forceinline__ void accumulate_range(AccF32<M, COMP, SHL>& A, const 
             }
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
-                if (gi == 0 && u == 0) feed_vec<M, DT, COMP, MAP, COMP, SHL>(A, xr[u], yr[u], c2, s2);
-                else feed_vec<M, DT, COMP, MAP, false, SHL>(A, xr[u], yr[u], c2, s2);
+                if (gi == 0 && u == 0) feed_vec<M, DT, COMP, MAP, COMP, SHL, CHEB>(A, xr[u], yr[u], c2, s2);
+                else feed_vec<M, DT, COMP, MAP, false, SHL, CHEB>(A, xr[u], yr[u], c2, s2);
             }
         }
         A.fold();
     }
     for (; v < nvec; v += nthreads) {
-        feed_vec<M, DT, COMP, MAP, COMP, SHL>(A, ld_stream16(xv + v), ld_stream16(yv + v), c2, s2);
+        feed_vec<M, DT, COMP, MAP, COMP, SHL, CHEB>(A, ld_stream16(xv + v), ld_stream16(yv + v), c2, s2);
         A.fold();
     }
     // scalar points: [b, b + head) and [b + head + nvec * PV, e)
@@ -806,7 +919,7 @@ __device__ __forceinline__ void accumulate_range(AccF32<M, COMP, SHL>& A, const 
         float xs = Elem<DT>::ld(x, i);
         const float ys = Elem<DT>::ld(y, i);
         if (MAP) xs = __fmul_rn(__fsub_rn(xs, cf), sf);
-        A.template add_pair<COMP>(pk2(xs, 0.0f), pk2(ys, 0.0f));
+        A.template add_pair<COMP>(pk2(xs, 0.0f), pk2(ys, 0.0f), pk2(1.0f, 0.0f));
         A.fold();
     }
 }
@@ -832,8 +945,8 @@ __device__ __forceinline__ void unpack_f64(uint4 r, double* v) {
     }
 }
 
-template <int M, int DT, int UNROLL, bool MAP>
-__device__ __forceinline__ void accumulate_range_f64(AccF64<M>& A, const void* x, const void* y,
+template <int M, int DT, int UNROLL, bool MAP, bool CHEB = false>
+__device__ __forceinline__ void accumulate_range_f64(AccF64<M, CHEB>& A, const void* x, const void* y,
                                                      int64_t b, int64_t e, int64_t rank,
                                                      int64_t nthreads, double c, double s) {
     constexpr int ES = Elem<DT>::kSize, PV = Elem<DT>::kPerVec;

@@ -273,99 +273,6 @@ __device__ __forceinline__ void accumulate_range_gen_f64(AccGenF64<M, W, CHEB>& 
     }
 }
 
-// Monomial coefficients of sum_k a_k T_k(t) (k <= m): the recurrence of the
-// basis applied to coefficient rows, P_{k+1}(t) = 2 t P_k(t) - P_{k-1}(t).
-template <int NMAX>
-__device__ __forceinline__ void cheb_to_mono(int m, const double* a, double* out) {
-    constexpr int N = NMAX + 1;
-    double pm1[N], p[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-        pm1[j] = j == 0 ? 1.0 : 0.0;
-        p[j] = j == 1 ? 1.0 : 0.0;
-        out[j] = a[0] * pm1[j] + (m >= 1 ? a[1] * p[j] : 0.0);
-    }
-#pragma unroll
-    for (int k = 2; k < N; ++k) {
-        if (k > m) break;
-#pragma unroll
-        for (int j = N - 1; j >= 0; --j) {
-            const double nj = (j > 0 ? 2.0 * p[j - 1] : 0.0) - pm1[j];
-            pm1[j] = p[j];
-            p[j] = nj;
-            out[j] = fma(a[k], nj, out[j]);
-        }
-    }
-}
-
-// Solve of the generalised normal equations from the moments Mo[0..2m] and
-// right-hand sides T[0..m] (count = number of points).  Monomial basis:
-// G[j][k] = Mo[j+k]; Chebyshev: G[j][k] = (Mo[j+k] + Mo[|j-k|]) / 2.
-// Singular when a pivot is at or below (m+1) * eps * max|G|.  Writes Xb (the
-// coefficients in the basis of t) and X (monomials of x), NaN on failure.
-template <int NMAX, bool CHEB>
-__device__ int solve_general_rt(int m, const double* Mo, const double* T, double count, double c, double s,
-                                bool map_ok, double eps, double* Xb, double* X, int ncoef) {
-    constexpr int N = NMAX + 1;
-    int st = LSEFIT_OK;
-    if (!map_ok) st = LSEFIT_ERR_BAD_INTERVAL;
-    else if (!(count >= (double)(m + 1))) st = LSEFIT_ERR_N_TOO_SMALL;
-    if (st == LSEFIT_OK) {
-        bool fin = true;
-        for (int k = 0; k <= 2 * m; ++k) fin = fin && isfinite(Mo[k]);
-        for (int k = 0; k <= m; ++k) fin = fin && isfinite(T[k]);
-        if (!fin) st = LSEFIT_ERR_NONFINITE;
-    }
-    double z[N];
-    if (st == LSEFIT_OK) {
-        double A[N][N + 1];
-        double amax = 0.0;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-                double g = (j == k) ? 1.0 : 0.0;
-                if (j <= m && k <= m) {
-                    g = CHEB ? 0.5 * (Mo[j + k] + Mo[j > k ? j - k : k - j]) : Mo[j + k];
-                    amax = fmax(amax, fabs(g));
-                }
-                A[j][k] = g;
-            }
-            A[j][N] = (j <= m) ? T[j] : 0.0;
-        }
-        st = ge_padded<NMAX>(m, A, (double)(m + 1) * eps * amax, z);
-    }
-    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
-    if (st != LSEFIT_OK) {
-        for (int i = 0; i < ncoef; ++i) {
-            const double v = i <= m ? qnan : 0.0;
-            if (Xb) Xb[i] = v;
-            X[i] = v;
-        }
-        return st;
-    }
-    double zt[N], out[N];
-    if (CHEB) {
-        cheb_to_mono<NMAX>(m, z, zt);
-    } else {
-#pragma unroll
-        for (int j = 0; j < N; ++j) zt[j] = z[j];
-    }
-    unmap_padded<NMAX>(m, zt, c, s, out);
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-        if (i < ncoef) {
-            if (Xb) Xb[i] = i <= m ? z[i] : 0.0;
-            X[i] = i <= m ? out[i] : 0.0;
-        }
-    }
-    for (int i = N; i < ncoef; ++i) {
-        if (Xb) Xb[i] = 0.0;
-        X[i] = 0.0;
-    }
-    return LSEFIT_OK;
-}
-
 // ---------------------------------------------------------------------------
 // Single-series kernels (as the power-sum pass: per-block partials in FP64,
 // the last block combines them in a fixed order and solves).

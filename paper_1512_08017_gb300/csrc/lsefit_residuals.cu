@@ -368,6 +368,7 @@ extern "C" int lsefit_residuals(const lsefit_batch* batch, const lsefit_plan* pl
     if (b.num_series != plan->num_series || b.m_max != plan->m_max || b.m_max < 1 || b.m_max > LSEFIT_MAX_DEGREE)
         return LSEFIT_ERR_INVALID_ARG;
     if (b.dtype < LSEFIT_F64 || b.dtype > LSEFIT_BF16) return LSEFIT_ERR_INVALID_ARG;
+    if (b.basis != LSEFIT_BASIS_MONOMIAL) return LSEFIT_ERR_UNSUPPORTED;  // evaluates t^k polynomials
     if (b.num_series == 0) return LSEFIT_OK;
     if (b.offsets == nullptr || b.degree == nullptr) return LSEFIT_ERR_INVALID_ARG;
     if (plan->total_points > 0 && (b.x == nullptr || b.y == nullptr)) return LSEFIT_ERR_INVALID_ARG;

@@ -60,7 +60,7 @@ class Batch(ctypes.Structure):
     _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
                 ("degree", ctypes.c_void_p), ("interval", ctypes.c_void_p),
                 ("num_series", ctypes.c_int64), ("m_max", ctypes.c_int32),
-                ("dtype", ctypes.c_int32), ("accum", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("dtype", ctypes.c_int32), ("accum", ctypes.c_int32), ("basis", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):
@@ -425,12 +425,16 @@ def _to_device(a, dtype, device):
 
 
 def fit_batched(x, y, offsets, degree, interval=None, m_max: int | None = None, accum="comp",
-                plan: BatchPlan | None = None, out: dict | None = None, stream=None) -> dict:
+                plan: BatchPlan | None = None, out: dict | None = None, stream=None, basis: str = "monomial") -> dict:
     """Fit every series of a ragged batch (lsefit_fit_batched), one persistent launch.
 
     x, y: 1-D CUDA tensors (float32/bfloat16/float64), all series concatenated.
     offsets: int64 [S+1]; degree: int32 [S]; interval: float64 [S, 2] or None.
-    Host arrays are copied to the device.  Returns dict(X, Xt, sums, map, status, plan)."""
+    Host arrays are copied to the device.  basis: "monomial" (the paper's fit)
+    or "chebyshev" (Xt then holds the Chebyshev coefficients of t).
+    Returns dict(X, Xt, sums, map, status, plan)."""
+    if basis not in BASES:
+        raise ValueError(f"basis must be one of {sorted(BASES)}")
     if not (isinstance(x, torch.Tensor) and x.is_cuda and isinstance(y, torch.Tensor) and y.is_cuda):
         raise ValueError("x and y must be CUDA tensors")
     if x.dim() != 1 or x.shape != y.shape or x.dtype != y.dtype:
@@ -459,7 +463,7 @@ def fit_batched(x, y, offsets, degree, interval=None, m_max: int | None = None, 
                "map": torch.empty(S, 2, dtype=torch.float64, device=dev),
                "status": torch.empty(S, dtype=torch.int32, device=dev)}
     b = Batch(x.data_ptr(), y.data_ptr(), off_d.data_ptr(), deg_d.data_ptr(),
-              iv.data_ptr() if iv is not None else None, S, m_max, _dtype_code(x), _accum_code(accum), 0)
+              iv.data_ptr() if iv is not None else None, S, m_max, _dtype_code(x), _accum_code(accum), BASES[basis])
     sh = _stream_handle(stream)
     ws = workspace("batched", plan.workspace_bytes, dev, sh)
     rc = lib.lsefit_fit_batched(ctypes.byref(b), ctypes.byref(plan.plan), _ptr(out["X"]), _ptr(out.get("Xt")),
@@ -467,6 +471,7 @@ def fit_batched(x, y, offsets, degree, interval=None, m_max: int | None = None, 
                                 _ptr(ws), ws.numel(), ctypes.c_void_p(sh))
     _check(rc, "lsefit_fit_batched")
     out["plan"] = plan
+    out["basis"] = basis
     # keep the device copies alive for asynchronous use
     out["_inputs"] = (off_d, deg_d, iv)
     return out
@@ -489,7 +494,7 @@ def residuals_batched(x, y, offsets, degree, fwd: dict, want_r: bool = False, wa
         out["r"] = torch.empty(x.shape, dtype=torch.float64 if x.dtype == torch.float64 else torch.float32,
                                device=dev)
     b = Batch(x.data_ptr(), y.data_ptr(), off_d.data_ptr(), deg_d.data_ptr(), None, S, plan.m_max,
-              _dtype_code(x), 0, 0)
+              _dtype_code(x), 0, BASES[fwd.get("basis", "monomial")])
     sh = _stream_handle(stream)
     ws = workspace("residuals", lib.lsefit_residuals_workspace_size(ctypes.byref(plan.plan)), dev, sh)
     rc = lib.lsefit_residuals(ctypes.byref(b), ctypes.byref(plan.plan), _ptr(fwd["Xt"]),
@@ -540,7 +545,7 @@ def backward(x, y, offsets, degree, fwd: dict, gX: torch.Tensor, interval_given:
     if status is None:
         status = torch.empty(S, dtype=torch.int32, device=dev)
     b = Batch(x.data_ptr(), y.data_ptr(), off_d.data_ptr(), deg_d.data_ptr(), None, S, plan.m_max,
-              _dtype_code(x), _accum_code(accum), 0)
+              _dtype_code(x), _accum_code(accum), BASES[fwd.get("basis", "monomial")])
     sh = _stream_handle(stream)
     nbytes = lib.lsefit_backward_workspace_size(ctypes.byref(plan.plan))
     ws = workspace("backward", nbytes, dev, sh)

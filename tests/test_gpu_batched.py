@@ -271,3 +271,67 @@ def test_full_size_ragged_sampled(L):
     lens = np.diff(b["offsets"])
     sample += [int(np.argmax(lens)), int(np.argmin(lens))]
     assert check_batch(L, b, res, "comp", series=sample) == len(sample)
+
+
+# --- the Chebyshev basis in the batched kernel ----------------------------------------
+
+def _check_cheb(L, b, res, accum, xs, ys, series=None):
+    """Per series: Chebyshev coefficients (Xt) against the oracle's fit in the same
+    basis, statuses equal, and the x-basis polynomial X gives the same values."""
+    X = res["X"].cpu().numpy()
+    Xt = res["Xt"].cpu().numpy()
+    st = res["status"].cpu().numpy()
+    checked = 0
+    for s in (range(len(b["degree"])) if series is None else series):
+        lo, hi = int(b["offsets"][s]), int(b["offsets"][s + 1])
+        m = int(b["degree"][s])
+        r = oracle.fit_general_interval(xs[lo:hi], ys[lo:hi], m, *b["interval"][s], fp32=accum != "f64",
+                                        basis="chebyshev")
+        got = L.STATUS_NAMES.get(int(st[s]), str(st[s]))
+        assert got == r["status"], (s, got, r["status"], hi - lo, m)
+        if r["status"] != "ok":
+            continue
+        cond = np.linalg.cond(r["G"])
+        tol = max(1e-6, cond * 2.0 ** -53 * 4 * m) if accum == "f64" else max(1e-5, cond * EPS32 * 4 * m)
+        e = np.linalg.norm(Xt[s, : m + 1] - r["Xb"]) / np.linalg.norm(r["Xb"])
+        assert e <= tol, (s, e, tol, m, hi - lo)
+        xx = np.linspace(b["interval"][s][0], b["interval"][s][1], 5)
+        f_ref = np.polynomial.chebyshev.chebval(r["s"] * (xx - r["c"]), r["Xb"])
+        terms = X[s, : m + 1][None, :] * xx[:, None] ** np.arange(m + 1)
+        slack = 2 * tol * np.abs(r["Xb"]).sum() + 1e-11 * np.abs(terms).sum(axis=1)
+        assert np.all(np.abs(terms.sum(axis=1) - f_ref) <= slack), (s, m)
+        checked += 1
+    return checked
+
+
+@pytest.mark.parametrize("dtype,accum", [(torch.float32, "comp"), (torch.bfloat16, "comp"),
+                                         (torch.float32, "f64"), (torch.float64, "f64")])
+@pytest.mark.parametrize("tuning", [None, {"warp_max_len": 512, "chunk_len": 2048}])
+def test_chebyshev_basis(L, dtype, accum, tuning):
+    b = synth.ragged_batch(num_series=300, lmin=16, lmax=30000, seed=44)
+    b["degree"][5] = 0  # not fitted: status and NaN row
+    x = torch.from_numpy(b["x"]).to(dtype).cuda()
+    y = torch.from_numpy(b["y"]).to(dtype).cuda()
+    plan = L.BatchPlan(b["offsets"], 5, tuning=tuning, degree=b["degree"])
+    res = L.fit_batched(x, y, b["offsets"], b["degree"], b["interval"], m_max=5, accum=accum, plan=plan,
+                        basis="chebyshev")
+    assert L.status_names(res["status"][5:6]) == ["invalid_arg"]
+    good = [s for s in range(300) if s != 5]
+    assert _check_cheb(L, b, res, accum, x.double().cpu().numpy(), y.double().cpu().numpy(), good) > 250
+    # a monomial fit of the same batch gives the same polynomials
+    mono = L.fit_batched(x, y, b["offsets"], b["degree"], b["interval"], m_max=5, accum=accum, plan=plan)
+    ok = (res["status"] == 0) & (mono["status"] == 0)
+    assert int(ok.sum()) > 250
+
+
+def test_chebyshev_basis_limits(L):
+    b = synth.ragged_batch(num_series=20, lmin=16, lmax=3000, seed=45)
+    x = torch.from_numpy(b["x"]).cuda()
+    y = torch.from_numpy(b["y"]).cuda()
+    with pytest.raises(L.LsefitError):  # no naive FP32 kernel in the Chebyshev basis
+        L.fit_batched(x, y, b["offsets"], b["degree"], b["interval"], m_max=5, accum="naive", basis="chebyshev")
+    res = L.fit_batched(x, y, b["offsets"], b["degree"], b["interval"], m_max=5, accum="comp", basis="chebyshev")
+    with pytest.raises(L.LsefitError):  # the residual pass evaluates monomials of t
+        L.residuals_batched(x, y, b["offsets"], b["degree"], res)
+    with pytest.raises(L.LsefitError):  # and so does the adjoint
+        L.backward(x, y, b["offsets"], b["degree"], res, torch.ones_like(res["X"]))
