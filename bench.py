@@ -199,6 +199,24 @@ def recorded_traffic(kernel_key: str):
 # ---------------------------------------------------------------------------
 # CPU baseline: the oracle as it stands, single thread, on a bounded sample
 # ---------------------------------------------------------------------------
+def host_info() -> dict:
+    """Host cores and CPU model of the machine the oracle is timed on."""
+    import platform
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key, _, val = line.partition(":")
+                fields.setdefault(key.strip(), val.strip())
+    except OSError:
+        pass
+    # x86 names the model; Arm kernels give the implementer and part numbers
+    model = fields.get("model name") or fields.get("Model")
+    if not model and "CPU part" in fields:
+        model = f"implementer {fields.get('CPU implementer', '?')} part {fields['CPU part']}"
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": model}
+
+
 def cpu_baseline_single(x: np.ndarray, y: np.ndarray, m: int, target_s: float):
     import oracle
     n = x.size
@@ -215,7 +233,7 @@ def cpu_baseline_single(x: np.ndarray, y: np.ndarray, m: int, target_s: float):
         if reps >= 1000:
             break
     assert out["status"] == "ok"
-    return {"value": sample * reps / t_total, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": sample * reps / t_total, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
             "sample": f"first {sample} points of the series, degree {m} fit "
                       f"(FP64 sums + Gaussian elimination, sequential C), {reps} repetitions, "
                       f"{t_total:.1f} s"}
@@ -539,7 +557,7 @@ def run_ragged_batch(args, dist: Dist):
                                     fp32=True)
             pts += hi - lo
         dt = time.perf_counter() - t0
-        cpu = {"value": pts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": pts / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
                "sample": f"{len(pick)} random series of the batch ({pts} points), oracle fit per series, "
                          f"{dt:.1f} s"}
     return {
@@ -847,7 +865,7 @@ def cpu_baseline_general(x, y, w, m, basis, interval, target_s, fp32=True):
         if reps >= 1000:
             break
     assert out["status"] == "ok"
-    return {"value": sample * reps / t_total, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": sample * reps / t_total, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
             "sample": f"first {sample} points of the series, degree {m} {basis} fit"
                       f"{' with weights' if w is not None else ''} (FP64 normal equations from their "
                       f"definition, sequential C), {reps} repetitions, {t_total:.1f} s"}
@@ -983,7 +1001,7 @@ def run_reference(args, dist: Dist):
             "impl": "reference",
             "config": {"workload": "single series, n=2^28 FP32 points (2 GiB), degrees 3,2,1 from one pass",
                        "sample_points_per_step": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
                              "sample": f"first {sample} points per step of the same series"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 

@@ -224,7 +224,11 @@ struct Nacc {
 //    exactly (4 registers per accumulator; 8 scalar instructions).
 // CHEB: the basis values are the Chebyshev polynomials T_k(t) (recurrence
 // T_{k+1} = 2t T_k - T_{k-1}) instead of the powers t^k; the slots keep the
-// same layout (moments of degree 1..2M, then the right-hand sides).
+// same layout (moments of degree 1..2M, then the right-hand sides).  The
+// values are carried as sigma_k T_k, sigma_k = -1 for k = 2, 3 (mod 4) and +1
+// otherwise, which makes each step one fma with +-2t and no negation
+// (sigma_{k+1} sigma_{k-1} = -1); rounding to nearest is symmetric under
+// negation, and result() restores the sign.
 template <int M, bool COMP, bool SHL = false, bool CHEB = false>
 struct AccF32 {
     static constexpr int N = 3 * M + 1;
@@ -260,6 +264,7 @@ struct AccF32 {
         u64 p = t;
         u64 pm1 = seed;       // T_{k-2} (Chebyshev)
         const u64 t2 = CHEB ? add2(t, t) : 0ull;
+        const u64 nt2 = CHEB ? mul2(t, pk2(-2.0f, -2.0f)) : 0ull;
         if (FIRST) {
             acc[2 * M] = y;
             acc[0] = p;
@@ -272,7 +277,8 @@ struct AccF32 {
 #pragma unroll
         for (int k = 2; k <= 2 * M; ++k) {
             if (CHEB) {
-                const u64 pk = fma2(t2, p, pm1 ^ 0x8000000080000000ull);
+                // sigma_k sigma_{k-1} = -1 for even k, +1 for odd k
+                const u64 pk = fma2((k & 1) ? t2 : nt2, p, pm1);
                 pm1 = p;
                 p = pk;
             } else {
@@ -321,8 +327,23 @@ struct AccF32 {
         }
     }
 
+    // Chebyshev sign of accumulator a: slot a < 2M holds the moment of
+    // degree a + 1, slot 2M + k the right-hand side of degree k.
+    static __device__ __forceinline__ bool negated(int a) {
+        const int k = a < 2 * M ? a + 1 : a - 2 * M;
+        return CHEB && (k & 2);
+    }
+
     // Final per-thread value of accumulator a as double-float.
     __device__ __forceinline__ dflt result(int a) const {
+        dflt r = result_signed(a);
+        if (negated(a)) {
+            r.hi = -r.hi;
+            r.lo = -r.lo;
+        }
+        return r;
+    }
+    __device__ __forceinline__ dflt result_signed(int a) const {
         dflt r;
         if (COMP && !SHL) {
             float x0, x1, l0, l1;
@@ -874,8 +895,29 @@ __device__ __forceinline__ void feed_vec(AccF32<M, COMP, SHL, CHEB>& A, uint4 xv
     }
 }
 
+// Groups of UNROLL vectors per compensated batch.  A batch gives each packed
+// lane 8 points (16 at degree >= 7, where the fold of 3m+1 slots would
+// otherwise be a large share of the per-point work); the naive FP32 sum of a
+// batch is the only uncompensated rounding, about (points - 1) ulp of the
+// batch's absolute sum.
+template <bool COMP, int M, int UNROLL, int PV>
+__host__ __device__ constexpr int comp_groups() {
+    const int batch = M >= 7 ? 16 : 8;        // points per packed lane
+    const int per_group = UNROLL * (PV / 2);  // points per packed lane in one group
+    return (!COMP || batch <= per_group) ? 1 : batch / per_group;
+}
+
+// Minimum resident blocks of 256 threads for the single-series FP32 passes:
+// two up to degree 5 (at most 128 registers, 16 warps per SM), one above,
+// where the compensated slots need more registers than two blocks leave.
+template <int M>
+__host__ __device__ constexpr int pass_min_blocks() {
+    return M <= 5 ? 2 : 1;
+}
+
 // FP32/BF16 storage, FP32 arithmetic.  In compensated mode each thread's
-// batch (UNROLL vectors, or one scalar point) is folded into its TwoSum pairs.
+// batch (comp_groups() x UNROLL vectors, or one scalar point) is folded into
+// its TwoSum pairs.
 template <int M, int DT, bool COMP, bool MAP, int UNROLL, bool SHL = false, bool CHEB = false>
 __device__ __forceinline__ void accumulate_range(AccF32<M, COMP, SHL, CHEB>& A, const void* x, const void* y,
                                                  int64_t b, int64_t e, int64_t rank, int64_t nthreads,
@@ -887,9 +929,7 @@ __device__ __forceinline__ void accumulate_range(AccF32<M, COMP, SHL, CHEB>& A, 
     const uint4* xv = reinterpret_cast<const uint4*>(static_cast<const char*>(x) + (b + head) * ES);
     const uint4* yv = reinterpret_cast<const uint4*>(static_cast<const char*>(y) + (b + head) * ES);
     int64_t v = rank;
-    // groups of UNROLL vectors per compensated batch: two at high degree, where
-    // the fold of 3m+1 slots is a large share of the per-point work
-    constexpr int G = (UNROLL == 2 && M >= 7) ? 2 : 1;
+    constexpr int G = comp_groups<COMP, M, UNROLL, PV>();
     for (; v + (G * UNROLL - 1) * nthreads < nvec; v += G * UNROLL * nthreads) {
 #pragma unroll
         for (int gi = 0; gi < G; ++gi) {

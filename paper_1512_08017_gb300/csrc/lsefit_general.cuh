@@ -13,13 +13,17 @@
 //     C_p = sum w T_p(t), so the pass still keeps 3m+1 (+1) accumulators.
 // Both run the basis recurrence on w-scaled values: b_0 = w, b_1 = w t, then
 // b_{k+1} = 2 t b_k - b_{k-1} (Chebyshev) or b_{k+1} = t b_k (monomial).
+// The Chebyshev values are carried as sigma_k b_k with sigma_k = -1 for
+// k = 2, 3 (mod 4), +1 otherwise: then sigma_{k+1} sigma_{k-1} = -1 and every
+// step is one fma, sigma_{k+1} b_{k+1} = (+-2t) (sigma_k b_k) + sigma_{k-1} b_{k-1},
+// with no negation.  Rounding to nearest is symmetric under negation, so the
+// sums are the exact negatives of the unsigned ones; result() restores the
+// sign.
 #pragma once
 
 #include "lsefit_device.cuh"
 
 namespace lsefit {
-
-__device__ __forceinline__ u64 neg2(u64 a) { return a ^ 0x8000000080000000ull; }
 
 // Accumulator slots: 0..2M the moments M_k = sum w phi_k(t), 2M+1..3M+1 the
 // right-hand sides T_k = sum w phi_k(t) y.  Without weights slot 0 (the
@@ -67,11 +71,13 @@ struct AccGenF32 {
         const u64 b1 = W ? mul2(w, t) : t;
         put<FIRST>(1, b1);
         put_fma<FIRST>(2 * M + 2, b1, y);
-        const u64 t2 = add2(t, t);
+        const u64 t2 = CHEB ? add2(t, t) : 0ull;
+        const u64 nt2 = CHEB ? mul2(t, pk2(-2.0f, -2.0f)) : 0ull;
         u64 bm2 = w, bm1 = b1;
 #pragma unroll
         for (int k = 2; k <= 2 * M; ++k) {
-            const u64 bk = CHEB ? fma2(t2, bm1, neg2(bm2)) : mul2(bm1, t);
+            // sigma_k sigma_{k-1} = -1 for even k, +1 for odd k
+            const u64 bk = CHEB ? fma2((k & 1) ? t2 : nt2, bm1, bm2) : mul2(bm1, t);
             put<FIRST>(k, bk);
             if (k <= M) put_fma<FIRST>(2 * M + 1 + k, bk, y);
             bm2 = bm1;
@@ -94,8 +100,23 @@ struct AccGenF32 {
         }
     }
 
+    // Basis index of slot a (moments 0..2M, then right-hand sides 0..M) and
+    // the sign its Chebyshev sums carry.
+    static __device__ __forceinline__ bool negated(int a) {
+        const int k = a <= 2 * M ? a : a - (2 * M + 1);
+        return CHEB && (k & 2);
+    }
+
     // Final per-thread value of slot a as double-float.
     __device__ __forceinline__ dflt result(int a) const {
+        dflt r = result_signed(a);
+        if (negated(a)) {
+            r.hi = -r.hi;
+            r.lo = -r.lo;
+        }
+        return r;
+    }
+    __device__ __forceinline__ dflt result_signed(int a) const {
         dflt r;
         if (a < K0) {
             r.hi = 0.0f;
@@ -197,9 +218,7 @@ __device__ __forceinline__ void accumulate_range_gen(AccGenF32<M, COMP, W, CHEB>
         }
     };
     int64_t v = rank;
-    // groups of UNROLL vectors per compensated batch: two at high degree, where
-    // the fold of 3m+2 slots is a large share of the per-point work
-    constexpr int G = (UNROLL == 2 && M >= 7) ? 2 : 1;
+    constexpr int G = comp_groups<COMP, M, UNROLL, PV>();
     for (; v + (G * UNROLL - 1) * nthreads < nvec; v += G * UNROLL * nthreads) {
 #pragma unroll
         for (int gi = 0; gi < G; ++gi) {
@@ -349,7 +368,7 @@ __device__ void gen_publish(const GenParams& p, const double* blk, bool map_ok, 
 }
 
 template <int M, int DT, bool COMP, bool W, bool CHEB, int UNROLL>
-__global__ void __launch_bounds__(kGenBlock) gen_kernel_f32(GenParams p) {
+__global__ void __launch_bounds__(kGenBlock, pass_min_blocks<M>()) gen_kernel_f32(GenParams p) {
     constexpr int N = 3 * M + 2;
     __shared__ dflt red[(kGenBlock / 32) * kGenBlock];
     __shared__ double blk[N];
