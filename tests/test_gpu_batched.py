@@ -324,6 +324,23 @@ def test_chebyshev_basis(L, dtype, accum, tuning):
     assert int(ok.sum()) > 250
 
 
+@pytest.mark.parametrize("dtype,accum", [(torch.float32, "comp"), (torch.bfloat16, "comp"),
+                                         (torch.float32, "f64")])
+def test_chebyshev_basis_high_degrees(L, dtype, accum):
+    """Degrees 1..8 in one batch (the m_max = 8 kernel), in block and warp tasks."""
+    # intervals wide enough for BF16 abscissae to stay distinct at degree 8
+    b = synth.ragged_batch(num_series=120, lmin=64, lmax=30000, mmin=1, mmax=8, seed=46,
+                           a_range=(-5.0, 5.0), w_range=(1.0, 8.0))
+    x = torch.from_numpy(b["x"]).to(dtype).cuda()
+    y = torch.from_numpy(b["y"]).to(dtype).cuda()
+    plan = L.BatchPlan(b["offsets"], 8, tuning={"warp_max_len": 2048, "chunk_len": 8192}, degree=b["degree"])
+    assert len(plan.block_tasks_host) > 0 and len(plan.warp_tasks_host) > 0
+    res = L.fit_batched(x, y, b["offsets"], b["degree"], b["interval"], m_max=8, accum=accum, plan=plan,
+                        basis="chebyshev")
+    assert _check_cheb(L, b, res, accum, x.double().cpu().numpy(), y.double().cpu().numpy()) > 100
+    assert {int(m) for m in b["degree"]} == set(range(1, 9))
+
+
 def test_chebyshev_basis_limits(L):
     b = synth.ragged_batch(num_series=20, lmin=16, lmax=3000, seed=45)
     x = torch.from_numpy(b["x"]).cuda()

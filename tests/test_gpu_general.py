@@ -96,7 +96,7 @@ def test_chebyshev_unscaled_interval(L, accum, m):
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float64])
-@pytest.mark.parametrize("m", [2, 6])
+@pytest.mark.parametrize("m", [2, 5, 6, 8])
 def test_weighted_chebyshev_storage(L, dtype, m):
     n = 300_001
     d = synth.small_series(n, seed=70 + m, lo=-3.0, hi=5.0, m=m, dtype=np.float64)
