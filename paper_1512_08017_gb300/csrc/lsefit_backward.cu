@@ -78,7 +78,7 @@ __global__ void lambda_kernel(int64_t S, int m_max, double eps, const int32_t* d
         sc = map[2 * s + 1];
         ok = isfinite(c) && isfinite(sc) && sc != 0.0;
     }
-    int st = fit_precheck(m, Srow, Srow + 2 * m + 1, ok);
+    int st = fit_precheck<NMAX>(m, Srow, Srow + 2 * m + 1, ok);
     constexpr int N = NMAX + 1;
     double gt[N], z[N];
     if (st == LSEFIT_OK) {
@@ -111,7 +111,7 @@ __global__ void lambda_kernel(int64_t S, int m_max, double eps, const int32_t* d
         }
         bool fin = true;
 #pragma unroll
-        for (int k = 0; k < N; ++k) fin = fin && isfinite(gt[k]);
+        for (int k = 0; k < N; ++k) fin = fin && finite_bits(gt[k]);
         st = fin ? hankel_ge<NMAX>(m, Srow, gt, z, eps) : LSEFIT_ERR_NONFINITE;
     }
     if (st == LSEFIT_OK) {

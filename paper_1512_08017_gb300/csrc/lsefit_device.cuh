@@ -541,12 +541,27 @@ __host__ __device__ constexpr double singular_eps(int accum) {
     return accum == LSEFIT_ACCUM_F64 ? 2.220446049250313e-16 : 1.1920928955078125e-07;
 }
 
-// Gaussian elimination with partial pivoting of the padded system
-// [[A, 0], [0, I]] z = [rhs, 0] with A[j][k] = S[j+k] (j, k <= m).
-// Returns LSEFIT_OK or LSEFIT_ERR_SINGULAR; z[0..m] is the solution.
+// Comparisons of FP64 values on the integer pipe (an FP64 instruction costs
+// ~78 cycles per warp on this part, an integer one ~2): the bit pattern of |v|
+// orders like |v| for every non-NaN double, and v is finite exactly when that
+// pattern is below the one of infinity.
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ bool finite_bits(double v) {
+    return abs_bits(v) < 0x7ff0000000000000ull;
+}
+// max(acc, |v|) for finite v as bit patterns (acc starts at 0, i.e. +0.0)
+__device__ __forceinline__ unsigned long long max_abs_bits(unsigned long long acc, double v) {
+    const unsigned long long b = abs_bits(v);
+    return b > acc ? b : acc;
+}
+
 // Gaussian elimination with partial pivoting of the padded system A z = r
 // (A[.][N] holds r; rows and columns beyond m are the identity), then back
-// substitution.  A pivot of a row <= m at or below tol is singular.
+// substitution.  The pivot is the first row of largest |a_rk|; a pivot of a
+// row <= m at or below tol is singular.  Returns LSEFIT_OK or
+// LSEFIT_ERR_SINGULAR; z[0..m] is the solution.
 template <int NMAX>
 __device__ __forceinline__ int ge_padded(int m, double (&A)[NMAX + 1][NMAX + 2], double tol, double* z) {
     constexpr int N = NMAX + 1;
@@ -555,16 +570,16 @@ __device__ __forceinline__ int ge_padded(int m, double (&A)[NMAX + 1][NMAX + 2],
 #pragma unroll
     for (int k = 0; k < N; ++k) {
         int p = k;
-        double best = fabs(A[k][k]);
+        unsigned long long best = abs_bits(A[k][k]);
 #pragma unroll
         for (int r = k + 1; r < N; ++r) {
-            const double v = fabs(A[r][k]);
+            const unsigned long long v = abs_bits(A[r][k]);
             if (v > best) {
                 best = v;
                 p = r;
             }
         }
-        if (k <= m && !(best > tol)) st = LSEFIT_ERR_SINGULAR;
+        if (k <= m && !(__longlong_as_double((long long)best) > tol)) st = LSEFIT_ERR_SINGULAR;
 #pragma unroll
         for (int r = k + 1; r < N; ++r) {
             if (r == p) {
@@ -596,7 +611,7 @@ __device__ __forceinline__ int ge_padded(int m, double (&A)[NMAX + 1][NMAX + 2],
         bool zf = true;
 #pragma unroll
         for (int i = 0; i < N; ++i)
-            if (i <= m) zf = zf && isfinite(z[i]);
+            if (i <= m) zf = zf && finite_bits(z[i]);
         if (!zf) st = LSEFIT_ERR_SINGULAR;
     }
     return st;
@@ -607,10 +622,12 @@ __device__ __forceinline__ int hankel_ge(int m, const double* S, const double* r
     constexpr int N = NMAX + 1;
     double A[N][N + 1];
     // max|A| over the 2m+1 distinct entries S_0..S_2m of the Hankel matrix
-    double amax = 0.0;
+    // (finite: checked before the elimination)
+    unsigned long long ab = 0ull;
 #pragma unroll
     for (int k = 0; k <= 2 * NMAX; ++k)
-        if (k <= 2 * m) amax = fmax(amax, fabs(S[k]));
+        if (k <= 2 * m) ab = max_abs_bits(ab, S[k]);
+    const double amax = __longlong_as_double((long long)ab);
 #pragma unroll
     for (int j = 0; j < N; ++j) {
 #pragma unroll
@@ -627,11 +644,11 @@ __device__ __forceinline__ int hankel_ge(int m, const double* S, const double* r
 template <int NMAX>
 __device__ __forceinline__ int hankel_cholesky(int m, const double* S, const double* rhs, double* z, double eps) {
     constexpr int N = NMAX + 1;
-    double amax = 0.0;
+    unsigned long long ab = 0ull;
 #pragma unroll
     for (int k = 0; k <= 2 * NMAX; ++k)
-        if (k <= 2 * m) amax = fmax(amax, fabs(S[k]));
-    const double tol = (double)(m + 1) * eps * amax;
+        if (k <= 2 * m) ab = max_abs_bits(ab, S[k]);
+    const double tol = (double)(m + 1) * eps * __longlong_as_double((long long)ab);
     double Lm[N][N];
     double inv[N];
     int st = LSEFIT_OK;
@@ -671,19 +688,25 @@ __device__ __forceinline__ int hankel_cholesky(int m, const double* S, const dou
         bool zf = true;
 #pragma unroll
         for (int i = 0; i < N; ++i)
-            if (i <= m) zf = zf && isfinite(z[i]);
+            if (i <= m) zf = zf && finite_bits(z[i]);
         if (!zf) st = LSEFIT_ERR_SINGULAR;
     }
     return st;
 }
 
-// Checks that precede the elimination: interval, point count, finiteness.
+// Checks that precede the elimination: interval, point count, finiteness
+// (m <= NMAX; the loads of S and T are issued together).
+template <int NMAX>
 __device__ __forceinline__ int fit_precheck(int m, const double* S, const double* T, bool map_ok) {
     if (!map_ok) return LSEFIT_ERR_BAD_INTERVAL;
     if (!(S[0] >= (double)(m + 1))) return LSEFIT_ERR_N_TOO_SMALL;
     bool fin = true;
-    for (int k = 0; k <= 2 * m; ++k) fin = fin && isfinite(S[k]);
-    for (int k = 0; k <= m; ++k) fin = fin && isfinite(T[k]);
+#pragma unroll
+    for (int k = 0; k <= 2 * NMAX; ++k)
+        if (k <= 2 * m) fin = fin & finite_bits(S[k]);
+#pragma unroll
+    for (int k = 0; k <= NMAX; ++k)
+        if (k <= m) fin = fin & finite_bits(T[k]);
     return fin ? LSEFIT_OK : LSEFIT_ERR_NONFINITE;
 }
 
@@ -718,7 +741,7 @@ __device__ int solve_hankel_rt(int m, const double* S, const double* T, double c
                                bool map_ok, double eps, double* Xt, double* X, int ncoef, bool identity = false) {
     constexpr int N = NMAX + 1;
     double z[N];
-    int st = fit_precheck(m, S, T, map_ok);
+    int st = fit_precheck<NMAX>(m, S, T, map_ok);
     if (st == LSEFIT_OK) st = CHOL ? hankel_cholesky<NMAX>(m, S, T, z, eps) : hankel_ge<NMAX>(m, S, T, z, eps);
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
     if (st != LSEFIT_OK) {
@@ -789,14 +812,18 @@ __device__ int solve_general_rt(int m, const double* Mo, const double* T, double
     else if (!(count >= (double)(m + 1))) st = LSEFIT_ERR_N_TOO_SMALL;
     if (st == LSEFIT_OK) {
         bool fin = true;
-        for (int k = 0; k <= 2 * m; ++k) fin = fin && isfinite(Mo[k]);
-        for (int k = 0; k <= m; ++k) fin = fin && isfinite(T[k]);
+#pragma unroll
+        for (int k = 0; k <= 2 * NMAX; ++k)
+            if (k <= 2 * m) fin = fin & finite_bits(Mo[k]);
+#pragma unroll
+        for (int k = 0; k <= NMAX; ++k)
+            if (k <= m) fin = fin & finite_bits(T[k]);
         if (!fin) st = LSEFIT_ERR_NONFINITE;
     }
     double z[N];
     if (st == LSEFIT_OK) {
         double A[N][N + 1];
-        double amax = 0.0;
+        unsigned long long ab = 0ull;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
 #pragma unroll
@@ -804,13 +831,13 @@ __device__ int solve_general_rt(int m, const double* Mo, const double* T, double
                 double g = (j == k) ? 1.0 : 0.0;
                 if (j <= m && k <= m) {
                     g = CHEB ? 0.5 * (Mo[j + k] + Mo[j > k ? j - k : k - j]) : Mo[j + k];
-                    amax = fmax(amax, fabs(g));
+                    ab = max_abs_bits(ab, g);
                 }
                 A[j][k] = g;
             }
             A[j][N] = (j <= m) ? T[j] : 0.0;
         }
-        st = ge_padded<NMAX>(m, A, (double)(m + 1) * eps * amax, z);
+        st = ge_padded<NMAX>(m, A, (double)(m + 1) * eps * __longlong_as_double((long long)ab), z);
     }
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
     if (st != LSEFIT_OK) {
