@@ -92,6 +92,8 @@ def _load():
         lib.orc_fit_general.restype = ctypes.c_int
         lib.orc_cheb_to_mono.argtypes = [ctypes.c_int, dp, dp]
         lib.orc_cheb_to_mono.restype = None
+        lib.orc_residuals_general.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, i64, dp, dp]
+        lib.orc_residuals_general.restype = ctypes.c_double
         lib.orc_max_degree.argtypes = []
         lib.orc_max_degree.restype = ctypes.c_int
         _lib = lib
@@ -274,3 +276,18 @@ def fit_general_interval(x, y, m: int, lo: float, hi: float, fp32: bool, w=None,
     out["c"] = c
     out["s"] = s
     return out
+
+
+def residuals_general(x, y, Xb, basis: str = "monomial", cs=None):
+    """Residuals of the fit f = sum_k Xb[k] phi_k(t), t = s(x - c) when cs = (c, s):
+    returns (SSE, V^T r with (V^T r)_k = sum_i phi_k(t_i) r_i, r)."""
+    x = _f64(x)
+    y = _f64(y)
+    Xb = _f64(Xb)
+    m = Xb.size - 1
+    r = np.zeros_like(x)
+    vtr = np.zeros(m + 1)
+    mp = _f64(cs) if cs is not None else None
+    sse = _load().orc_residuals_general(m, BASES[basis], _ptr(Xb), _ptr(mp) if mp is not None else None,
+                                        _ptr(x), _ptr(y), x.size, _ptr(r), _ptr(vtr))
+    return float(sse), vtr, r

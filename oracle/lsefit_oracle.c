@@ -432,3 +432,28 @@ int orc_fit_general(const double* x, const double* y, const double* w, int64_t n
     else memcpy(X, Xt, sizeof(double) * N);
     return ORC_OK;
 }
+
+/*
+ * Residuals of a fit in the basis `basis` (Section III judges fits by their
+ * residual errors, Table V): r_i = y_i - sum_k Xb[k] phi_k(t_i) with
+ * t_i = s (x_i - c) (t_i = x_i without a map), SSE = sum_i r_i^2 (returned),
+ * vtr[k] = sum_i phi_k(t_i) r_i (k = 0..m), and r (length n) if r_out is set.
+ */
+double orc_residuals_general(int m, int basis, const double* Xb, const double* map, const double* x,
+                             const double* y, int64_t n, double* r_out, double* vtr)
+{
+    double phi[ORC_MAX_M + 1];
+    double sse = 0.0;
+    for (int k = 0; k <= m; ++k) vtr[k] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double t = map ? map[1] * (x[i] - map[0]) : x[i];
+        orc_basis(m, basis, t, phi);
+        double f = 0.0;
+        for (int k = 0; k <= m; ++k) f += Xb[k] * phi[k];
+        const double r = y[i] - f;
+        if (r_out) r_out[i] = r;
+        sse += r * r;
+        for (int k = 0; k <= m; ++k) vtr[k] += phi[k] * r;
+    }
+    return sse;
+}

@@ -58,6 +58,10 @@ MUTANTS = {
     "weight_dropped_rhs": ("b[j] += wi * phi[j] * y[i];", "b[j] += phi[j] * y[i];"),
     # Chebyshev-to-monomial expansion without the shift by one power
     "cheb_to_mono_shift": ("(j > 0 ? 2.0 * P[(k - 1) * N + j - 1] : 0.0)", "(j > 0 ? 2.0 * P[(k - 1) * N + j] : 0.0)"),
+    # residual diagnostics: V^T y accumulated instead of V^T r
+    "residual_vtr_operand": ("vtr[k] += phi[k] * r;", "vtr[k] += phi[k] * y[i];"),
+    # residual sign reversed (the SSE alone cannot see it)
+    "residual_sign": ("const double r = y[i] - f;", "const double r = f - y[i];"),
     # residual evaluation drops the constant term
     "eval_drop_a0": ("acc += X[j] * p;\n            p *= x[i];\n        }\n        f[i] = acc;",
                      "if (j) acc += X[j] * p;\n            p *= x[i];\n        }\n        f[i] = acc;"),

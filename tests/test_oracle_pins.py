@@ -539,3 +539,44 @@ def test_general_statuses():
     assert oracle.fit_general(x, x, 1, w=np.array([1.0, np.inf, 1.0]))["status"] == "nonfinite"
     assert oracle.fit_general(np.full(5, 0.3), np.arange(5.0), 1, basis="chebyshev")["status"] == "singular"
     assert oracle.fit_general_interval(x, x, 1, 1.0, 1.0, fp32=False)["status"] == "bad_interval"
+
+
+# --- residuals in either basis (Section III, Table V) -----------------------------------
+
+@pytest.mark.parametrize("basis", ["monomial", "chebyshev"])
+def test_residuals_general_against_numpy(basis):
+    """r, SSE and V^T r of an arbitrary polynomial against numpy's own evaluation
+    (polyval / chebval) and Vandermonde matrices (vander / chebvander)."""
+    rng = np.random.default_rng(1540)
+    x = rng.uniform(2.0, 9.0, 777)
+    y = rng.normal(size=x.size)
+    Xb = rng.normal(size=6)
+    c, s = 5.5, 2.0 / 7.0
+    t = s * (x - c)
+    if basis == "chebyshev":
+        f = np.polynomial.chebyshev.chebval(t, Xb)
+        V = np.polynomial.chebyshev.chebvander(t, 5)
+    else:
+        f = np.polynomial.polynomial.polyval(t, Xb)
+        V = np.vander(t, 6, increasing=True)
+    sse, vtr, r = oracle.residuals_general(x, y, Xb, basis, cs=(c, s))
+    np.testing.assert_allclose(r, y - f, rtol=0, atol=1e-13)
+    assert abs(sse - np.sum((y - f) ** 2)) <= 1e-12 * sse
+    np.testing.assert_allclose(vtr, V.T @ (y - f), rtol=0, atol=1e-11)
+
+
+def test_residuals_general_table1_and_orthogonality():
+    """Table I, m = 3: the SSE of the exact fit (128.1995754) in both bases, with
+    V^T r = 0 at the least-squares solution (the normal equations of Section II)."""
+    _, _, x, y = _table1()
+    cs = (np.mean(x), 2.0 / (x.max() - x.min()))
+    mono = oracle.fit(x, y, 3)
+    sse_m, vtr_m, _ = oracle.residuals_general(x, y, mono["X"], "monomial")
+    assert abs(sse_m - oracle.sse(mono["X"], x, y)) <= 1e-12 * sse_m
+    assert abs(sse_m - 128.1995754) <= 1e-6
+    cheb = oracle.fit_general(x, y, 3, basis="chebyshev", cs=cs)
+    sse_c, vtr_c, _ = oracle.residuals_general(x, y, cheb["Xb"], "chebyshev", cs=cs)
+    assert abs(sse_c - sse_m) <= 1e-9 * sse_m
+    scale = np.sum(np.abs(y)) * 1e3
+    assert np.max(np.abs(vtr_c)) <= 1e-12 * scale
+    assert np.max(np.abs(vtr_m[:1])) <= 1e-9 * scale
