@@ -516,16 +516,19 @@ def run_ragged_batch(args, dist: Dist):
     # the residual/SSE pass over the same batch (reads x, y once more: 8 B/point),
     # from a fit that also keeps the mapped-basis coefficients and the map
     residuals = None
-    if args.basis == "monomial":
-        fwd_full = L.fit_batched(x, y, off, deg, iv, m_max=m_max, accum=args.accum, plan=plan)
-        res_out = L.residuals_batched(x, y, off, deg, fwd_full)
-        torch.cuda.synchronize()
-        assert bool(torch.isfinite(res_out["sse"]).all())
-        rper, _ = _event_steps(lambda: L.residuals_batched(x, y, off, deg, fwd_full), args.steps, stream)
-        r_ms = dist.max(statistics.mean(rper))
-        residuals = {"ms_per_step": r_ms, "hbm_gbs": 8 * N / (r_ms / 1e3) / 1e9,
-                     "roofline": _roofline(8 * N, r_ms, "residuals_kernel<F32> (+ prep launch)", "residuals_f32"),
-                     "desc": "lsefit_residuals: SSE and V^T r per series from the fit's Xt and map"}
+    fwd_full = L.fit_batched(x, y, off, deg, iv, m_max=m_max, accum=args.accum, plan=plan, basis=args.basis)
+    res_out = L.residuals_batched(x, y, off, deg, fwd_full)
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(res_out["sse"]).all())
+    rper, _ = _event_steps(lambda: L.residuals_batched(x, y, off, deg, fwd_full), args.steps, stream)
+    r_ms = dist.max(statistics.mean(rper))
+    cheb = args.basis != "monomial"
+    residuals = {"ms_per_step": r_ms, "hbm_gbs": 8 * N / (r_ms / 1e3) / 1e9,
+                 "roofline": _roofline(8 * N, r_ms,
+                                       "residuals_kernel<F32{}> (+ prep launch)".format(",chebyshev" if cheb else ""),
+                                       "residuals_f32_chebyshev" if cheb else "residuals_f32"),
+                 "desc": "lsefit_residuals: SSE and V^T r per series from the fit's Xt and map"
+                         + (" (Clenshaw evaluation, T_k(t) r diagnostics)" if cheb else "")}
 
     e2e = None
     if not args.no_e2e:

@@ -434,11 +434,15 @@ size_t lsefit_residuals_workspace_size(const lsefit_plan* plan);
  * mapped abscissae t_i = s (x_i - c).  V^T r vanishes at the least-squares
  * solution (the normal equations of Section II), so it measures how well a
  * fit satisfies them.  FP32 per point, compensated double-float sums, FP64
- * chunk combine; FP64 throughout for FP64 data.
+ * chunk combine; FP64 throughout for FP64 data.  For a fit in the Chebyshev
+ * basis, f(t) = sum_k Xt_k T_k(t) (Clenshaw's recurrence) and
+ * (V^T r)_{s,k} = sum_i T_k(t_i) r_i.
  *  batch     as for lsefit_fit_batched (interval unused: the map is `map`);
- *            basis must be LSEFIT_BASIS_MONOMIAL (else LSEFIT_ERR_UNSUPPORTED).
+ *            basis as in the fit that produced Xt (LSEFIT_BASIS_MONOMIAL or
+ *            LSEFIT_BASIS_CHEBYSHEV, else LSEFIT_ERR_INVALID_ARG).
  *  plan      the layout's plan, device task arrays set.
- *  Xt        device double[num_series][m_max+1] (from lsefit_fit_batched).
+ *  Xt        device double[num_series][m_max+1] (from lsefit_fit_batched):
+ *            coefficients in the mapped basis, monomial or Chebyshev.
  *  map       device double[num_series][2] {c, s} or NULL (identity).
  *  r         device array like y or NULL: per-point residuals (FP32 for
  *            F32/BF16 data, FP64 for F64 data).

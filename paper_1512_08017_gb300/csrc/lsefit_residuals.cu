@@ -6,7 +6,10 @@
 // diagnostics (V^T r)_k = sum_i t_i^k r_i (k = 0..m), which vanish at the
 // least-squares solution (the normal equations of Section II), and
 // optionally the residuals themselves.  f is evaluated in the mapped basis:
-// f(x_i) = sum_k Xt_k t_i^k, t_i = s (x_i - c), by Horner's rule.
+// f(x_i) = sum_k Xt_k t_i^k, t_i = s (x_i - c), by Horner's rule.  For a fit
+// in the Chebyshev basis (CHEB), f = sum_k Xt_k T_k(t) by Clenshaw's
+// recurrence and the diagnostics are (V^T r)_k = sum_i T_k(t_i) r_i, with
+// T_k(t) r following the basis recurrence from r and t r.
 //
 // Accumulation: FP32 per point, compensated double-float per thread
 // (TwoSum per small batch), double-float warp/block reductions, FP64 chunk
@@ -40,8 +43,8 @@ struct RsParams {
     unsigned* counters;  // [0] block queue, [1] warp queue, [2] exited blocks
 };
 
-// Per-thread sums: a = 0 -> r^2, a = 1 + k -> t^k r.
-template <int M>
+// Per-thread sums: a = 0 -> r^2, a = 1 + k -> t^k r (T_k(t) r for CHEB).
+template <int M, bool CHEB>
 struct RsAcc {
     static constexpr int N = M + 2;
     float bh[N];  // batch sums
@@ -56,11 +59,25 @@ struct RsAcc {
     }
     __device__ __forceinline__ void add(float t, float r) {
         bh[0] = fmaf(r, r, bh[0]);
-        float p = r;
+        if (CHEB) {
+            const float t2 = t + t;
+            float qm = r, q = t * r;  // T_0 r, T_1 r
+            bh[1] += qm;
+            bh[2] += q;
 #pragma unroll
-        for (int k = 0; k <= M; ++k) {
-            bh[1 + k] += p;
-            p *= t;
+            for (int k = 2; k <= M; ++k) {
+                const float qn = fmaf(t2, q, -qm);
+                bh[1 + k] += qn;
+                qm = q;
+                q = qn;
+            }
+        } else {
+            float p = r;
+#pragma unroll
+            for (int k = 0; k <= M; ++k) {
+                bh[1 + k] += p;
+                p *= t;
+            }
         }
     }
     __device__ __forceinline__ void fold() {
@@ -75,11 +92,24 @@ struct RsAcc {
     }
 };
 
-template <int M>
-__device__ __forceinline__ float horner(const float* a, float t) {
-    float v = a[M];
+// f(t) = sum_k a_k t^k by Horner's rule, or sum_k a_k T_k(t) by Clenshaw's
+// recurrence b_k = a_k + 2t b_{k+1} - b_{k+2}, f = a_0 + t b_1 - b_2.
+template <int M, bool CHEB, typename F>
+__device__ __forceinline__ F eval_poly(const F* a, F t) {
+    if (CHEB) {
+        const F t2 = t + t;
+        F b1 = F(0), b2 = F(0);
 #pragma unroll
-    for (int j = M - 1; j >= 0; --j) v = fmaf(v, t, a[j]);
+        for (int k = M; k >= 1; --k) {
+            const F bk = fma(t2, b1, a[k] - b2);
+            b2 = b1;
+            b1 = bk;
+        }
+        return fma(t, b1, a[0] - b2);
+    }
+    F v = a[M];
+#pragma unroll
+    for (int j = M - 1; j >= 0; --j) v = fma(v, t, a[j]);
     return v;
 }
 
@@ -88,9 +118,9 @@ __device__ __forceinline__ float horner(const float* a, float t) {
 // point by point); compensated batch folded after every group of vectors.
 constexpr int kRsUnroll = 4;
 
-template <int DT, int M>
+template <int DT, int M, bool CHEB>
 __device__ __forceinline__ void rs_range_f32(const RsParams& p, int64_t s, int64_t b, int64_t e, int64_t rank,
-                                             int64_t nthreads, RsAcc<M>& A) {
+                                             int64_t nthreads, RsAcc<M, CHEB>& A) {
     constexpr int ES = Elem<DT>::kSize, PV = Elem<DT>::kPerVec, U = kRsUnroll;
     const int nc = p.m_max + 1;
     float coef[M + 1];
@@ -125,7 +155,7 @@ __device__ __forceinline__ void rs_range_f32(const RsParams& p, int64_t s, int64
 #pragma unroll
         for (int q = 0; q < PV; ++q) {
             const float t = __fmul_rn(__fsub_rn(xs[q], c), sc);
-            rr[q] = __fsub_rn(ys[q], horner<M>(coef, t));
+            rr[q] = __fsub_rn(ys[q], eval_poly<M, CHEB>(coef, t));
             A.add(t, rr[q]);
         }
         if (rout) {
@@ -161,14 +191,14 @@ __device__ __forceinline__ void rs_range_f32(const RsParams& p, int64_t s, int64
     for (int64_t q = rank; q < nscalar; q += nthreads) {
         const int64_t i = q < head ? b + q : tail0 + (q - head);
         const float t = __fmul_rn(__fsub_rn(Elem<DT>::ld(p.x, i), c), sc);
-        const float r = __fsub_rn(Elem<DT>::ld(p.y, i), horner<M>(coef, t));
+        const float r = __fsub_rn(Elem<DT>::ld(p.y, i), eval_poly<M, CHEB>(coef, t));
         if (rout) rout[i] = r;
         A.add(t, r);
     }
     A.fold();
 }
 
-template <int M>
+template <int M, bool CHEB>
 __device__ __forceinline__ void rs_range_f64(const RsParams& p, int64_t s, int64_t b, int64_t e, int64_t rank,
                                              int64_t nthreads, double* acc) {
     const int nc = p.m_max + 1;
@@ -180,17 +210,27 @@ __device__ __forceinline__ void rs_range_f64(const RsParams& p, int64_t s, int64
     double* rout = static_cast<double*>(p.r);
     for (int64_t i = b + rank; i < e; i += nthreads) {
         const double t = sc * (Elem<LSEFIT_F64>::ld64(p.x, i) - c);
-        double f = coef[M];
-#pragma unroll
-        for (int j = M - 1; j >= 0; --j) f = fma(f, t, coef[j]);
-        const double r = Elem<LSEFIT_F64>::ld64(p.y, i) - f;
+        const double r = Elem<LSEFIT_F64>::ld64(p.y, i) - eval_poly<M, CHEB>(coef, t);
         if (rout) rout[i] = r;
         acc[0] = fma(r, r, acc[0]);
-        double q = r;
+        if (CHEB) {
+            double qm = r, q = t * r;
+            acc[1] += qm;
+            acc[2] += q;
 #pragma unroll
-        for (int k = 0; k <= M; ++k) {
-            acc[1 + k] += q;
-            q *= t;
+            for (int k = 2; k <= M; ++k) {
+                const double qn = fma(t + t, q, -qm);
+                acc[1 + k] += qn;
+                qm = q;
+                q = qn;
+            }
+        } else {
+            double q = r;
+#pragma unroll
+            for (int k = 0; k <= M; ++k) {
+                acc[1 + k] += q;
+                q *= t;
+            }
         }
     }
 }
@@ -205,7 +245,7 @@ __device__ __forceinline__ void rs_store(const RsParams& p, int64_t s, int M, co
     }
 }
 
-template <int DT, int M>
+template <int DT, int M, bool CHEB>
 __device__ void rs_block_task(const RsParams& p, int t, int4 task, dflt* red, double* red64, double* tot,
                               int* s_last) {
     constexpr int N = M + 2;
@@ -219,12 +259,12 @@ __device__ void rs_block_task(const RsParams& p, int t, int4 task, dflt* red, do
         double acc[N];
 #pragma unroll
         for (int a = 0; a < N; ++a) acc[a] = 0.0;
-        rs_range_f64<M>(p, s, b, e, tid, kRsBlock, acc);
+        rs_range_f64<M, CHEB>(p, s, b, e, tid, kRsBlock, acc);
         block_reduce_d<kRsBlock, N>([&](int a) { return acc[a]; }, red64, tot);
     } else {
-        RsAcc<M> A;
+        RsAcc<M, CHEB> A;
         A.init();
-        rs_range_f32<DT, M>(p, s, b, e, tid, kRsBlock, A);
+        rs_range_f32<DT, M, CHEB>(p, s, b, e, tid, kRsBlock, A);
         block_reduce_df<kRsBlock, N>([&](int a) { dflt v = {A.hi[a], A.lo[a]}; return v; }, red, tot);
     }
     const bool ok = isfinite(p.Xt[s * (p.m_max + 1)]);
@@ -255,7 +295,7 @@ __device__ void rs_block_task(const RsParams& p, int t, int4 task, dflt* red, do
     }
 }
 
-template <int DT, int M>
+template <int DT, int M, bool CHEB>
 __device__ void rs_warp_task(const RsParams& p, int64_t s) {
     constexpr int N = M + 2;
     const int lane = threadIdx.x & 31;
@@ -265,13 +305,13 @@ __device__ void rs_warp_task(const RsParams& p, int64_t s) {
         double acc[N];
 #pragma unroll
         for (int a = 0; a < N; ++a) acc[a] = 0.0;
-        rs_range_f64<M>(p, s, b, e, lane, 32, acc);
+        rs_range_f64<M, CHEB>(p, s, b, e, lane, 32, acc);
 #pragma unroll
         for (int a = 0; a < N; ++a) tot[a] = warp_reduce_d(acc[a]);
     } else {
-        RsAcc<M> A;
+        RsAcc<M, CHEB> A;
         A.init();
-        rs_range_f32<DT, M>(p, s, b, e, lane, 32, A);
+        rs_range_f32<DT, M, CHEB>(p, s, b, e, lane, 32, A);
 #pragma unroll
         for (int a = 0; a < N; ++a) {
             const dflt v = {A.hi[a], A.lo[a]};
@@ -281,7 +321,7 @@ __device__ void rs_warp_task(const RsParams& p, int64_t s) {
     if (lane == 0) rs_store(p, s, M, tot, isfinite(p.Xt[s * (p.m_max + 1)]));
 }
 
-template <int DT>
+template <int DT, bool CHEB>
 __global__ void __launch_bounds__(kRsBlock) residuals_kernel(RsParams p) {
     __shared__ int s_task;
     __shared__ int s_last;
@@ -298,14 +338,14 @@ __global__ void __launch_bounds__(kRsBlock) residuals_kernel(RsParams p) {
         const int4 task = p.block_tasks[t];
         const int m = p.degree[task.x];
         switch (m) {
-            case 1: rs_block_task<DT, 1>(p, t, task, red, red64, tot, &s_last); break;
-            case 2: rs_block_task<DT, 2>(p, t, task, red, red64, tot, &s_last); break;
-            case 3: rs_block_task<DT, 3>(p, t, task, red, red64, tot, &s_last); break;
-            case 4: rs_block_task<DT, 4>(p, t, task, red, red64, tot, &s_last); break;
-            case 5: rs_block_task<DT, 5>(p, t, task, red, red64, tot, &s_last); break;
-            case 6: rs_block_task<DT, 6>(p, t, task, red, red64, tot, &s_last); break;
-            case 7: rs_block_task<DT, 7>(p, t, task, red, red64, tot, &s_last); break;
-            case 8: rs_block_task<DT, 8>(p, t, task, red, red64, tot, &s_last); break;
+            case 1: rs_block_task<DT, 1, CHEB>(p, t, task, red, red64, tot, &s_last); break;
+            case 2: rs_block_task<DT, 2, CHEB>(p, t, task, red, red64, tot, &s_last); break;
+            case 3: rs_block_task<DT, 3, CHEB>(p, t, task, red, red64, tot, &s_last); break;
+            case 4: rs_block_task<DT, 4, CHEB>(p, t, task, red, red64, tot, &s_last); break;
+            case 5: rs_block_task<DT, 5, CHEB>(p, t, task, red, red64, tot, &s_last); break;
+            case 6: rs_block_task<DT, 6, CHEB>(p, t, task, red, red64, tot, &s_last); break;
+            case 7: rs_block_task<DT, 7, CHEB>(p, t, task, red, red64, tot, &s_last); break;
+            case 8: rs_block_task<DT, 8, CHEB>(p, t, task, red, red64, tot, &s_last); break;
             default:
                 if (tid == 0 && task.y == 0) p.sse[task.x] = __longlong_as_double(0x7ff8000000000000ll);
                 break;
@@ -319,14 +359,14 @@ __global__ void __launch_bounds__(kRsBlock) residuals_kernel(RsParams p) {
         if (t >= p.n_warp_tasks) break;
         const int64_t s = p.warp_tasks[t].x;
         switch (p.degree[s]) {
-            case 1: rs_warp_task<DT, 1>(p, s); break;
-            case 2: rs_warp_task<DT, 2>(p, s); break;
-            case 3: rs_warp_task<DT, 3>(p, s); break;
-            case 4: rs_warp_task<DT, 4>(p, s); break;
-            case 5: rs_warp_task<DT, 5>(p, s); break;
-            case 6: rs_warp_task<DT, 6>(p, s); break;
-            case 7: rs_warp_task<DT, 7>(p, s); break;
-            case 8: rs_warp_task<DT, 8>(p, s); break;
+            case 1: rs_warp_task<DT, 1, CHEB>(p, s); break;
+            case 2: rs_warp_task<DT, 2, CHEB>(p, s); break;
+            case 3: rs_warp_task<DT, 3, CHEB>(p, s); break;
+            case 4: rs_warp_task<DT, 4, CHEB>(p, s); break;
+            case 5: rs_warp_task<DT, 5, CHEB>(p, s); break;
+            case 6: rs_warp_task<DT, 6, CHEB>(p, s); break;
+            case 7: rs_warp_task<DT, 7, CHEB>(p, s); break;
+            case 8: rs_warp_task<DT, 8, CHEB>(p, s); break;
             default:
                 if (lane == 0) p.sse[s] = __longlong_as_double(0x7ff8000000000000ll);
                 break;
@@ -368,7 +408,7 @@ extern "C" int lsefit_residuals(const lsefit_batch* batch, const lsefit_plan* pl
     if (b.num_series != plan->num_series || b.m_max != plan->m_max || b.m_max < 1 || b.m_max > LSEFIT_MAX_DEGREE)
         return LSEFIT_ERR_INVALID_ARG;
     if (b.dtype < LSEFIT_F64 || b.dtype > LSEFIT_BF16) return LSEFIT_ERR_INVALID_ARG;
-    if (b.basis != LSEFIT_BASIS_MONOMIAL) return LSEFIT_ERR_UNSUPPORTED;  // evaluates t^k polynomials
+    if (b.basis != LSEFIT_BASIS_MONOMIAL && b.basis != LSEFIT_BASIS_CHEBYSHEV) return LSEFIT_ERR_INVALID_ARG;
     if (b.num_series == 0) return LSEFIT_OK;
     if (b.offsets == nullptr || b.degree == nullptr) return LSEFIT_ERR_INVALID_ARG;
     if (plan->total_points > 0 && (b.x == nullptr || b.y == nullptr)) return LSEFIT_ERR_INVALID_ARG;
@@ -399,8 +439,10 @@ extern "C" int lsefit_residuals(const lsefit_batch* batch, const lsefit_plan* pl
     residuals_prep_kernel<<<(items + 255) / 256, 256, 0, (cudaStream_t)stream>>>(p.counters, p.tickets,
                                                                                plan->n_block_tasks);
     if (cudaGetLastError() != cudaSuccess) return LSEFIT_ERR_CUDA;
-    auto k = b.dtype == LSEFIT_F64 ? residuals_kernel<LSEFIT_F64>
-             : b.dtype == LSEFIT_F32 ? residuals_kernel<LSEFIT_F32> : residuals_kernel<LSEFIT_BF16>;
+    const bool cheb = b.basis == LSEFIT_BASIS_CHEBYSHEV;
+    auto k = b.dtype == LSEFIT_F64 ? (cheb ? residuals_kernel<LSEFIT_F64, true> : residuals_kernel<LSEFIT_F64, false>)
+             : b.dtype == LSEFIT_F32 ? (cheb ? residuals_kernel<LSEFIT_F32, true> : residuals_kernel<LSEFIT_F32, false>)
+                                     : (cheb ? residuals_kernel<LSEFIT_BF16, true> : residuals_kernel<LSEFIT_BF16, false>);
     int dev = 0;
     const int sms = current_sm_count(&dev);
     if (sms <= 0) return LSEFIT_ERR_CUDA;

@@ -64,6 +64,50 @@ def test_residuals_against_oracle(L, dtype, accum, tuning):
     assert checked > 120
 
 
+@pytest.mark.parametrize("dtype,accum", [(torch.float32, "comp"), (torch.float64, "f64"),
+                                         (torch.bfloat16, "comp")])
+@pytest.mark.parametrize("tuning", [None, {"warp_max_len": 256, "chunk_len": 4096}])
+def test_residuals_chebyshev_basis(L, dtype, accum, tuning):
+    """Chebyshev-basis fits of degrees 1..8: f by Clenshaw's recurrence and
+    (V^T r)_k = sum_i T_k(t_i) r_i, against the oracle's residuals of its own
+    Chebyshev fit of the same stored points."""
+    b = synth.ragged_batch(num_series=150, lmin=20, lmax=30000, mmin=1, mmax=8, seed=92,
+                           a_range=(-5.0, 5.0), w_range=(1.0, 8.0))
+    x = torch.from_numpy(b["x"]).to(dtype).cuda()
+    y = torch.from_numpy(b["y"]).to(dtype).cuda()
+    xs = x.double().cpu().numpy()
+    ys = y.double().cpu().numpy()
+    plan = L.BatchPlan(b["offsets"], 8, tuning=tuning, degree=b["degree"])
+    fwd = L.fit_batched(x, y, b["offsets"], b["degree"], b["interval"], m_max=8, accum=accum, plan=plan,
+                        basis="chebyshev")
+    out = L.residuals_batched(x, y, b["offsets"], b["degree"], fwd, want_r=True)
+    sse = out["sse"].cpu().numpy()
+    vtr = out["vtr"].cpu().numpy()
+    rr = out["r"].double().cpu().numpy()
+    tol = 1e-9 if dtype == torch.float64 else (1e-4 if dtype == torch.float32 else 1e-3)
+    checked = 0
+    for s in range(150):
+        lo, hi = int(b["offsets"][s]), int(b["offsets"][s + 1])
+        m = int(b["degree"][s])
+        if L.status_names(fwd["status"][s: s + 1]) != ["ok"]:
+            continue
+        r = oracle.fit_general_interval(xs[lo:hi], ys[lo:hi], m, *b["interval"][s], fp32=accum != "f64",
+                                        basis="chebyshev")
+        assert r["status"] == "ok", s
+        sse_ref, vtr_ref, res = oracle.residuals_general(xs[lo:hi], ys[lo:hi], r["Xb"], "chebyshev",
+                                                         cs=(r["c"], r["s"]))
+        t = r["s"] * (xs[lo:hi] - r["c"])
+        scale = np.abs(np.polynomial.chebyshev.chebvander(t, m)).T @ np.abs(ys[lo:hi])
+        assert abs(sse[s] - sse_ref) <= tol * sse_ref + 1e-30, (s, sse[s], sse_ref)
+        f = 8 * m * (2.0 ** -53 if accum == "f64" else 2.0 ** -24)
+        assert np.all(np.abs(vtr[s, : m + 1] - vtr_ref) <= 1e3 * f * scale + 1e-30), s
+        assert np.all(vtr[s, m + 1:] == 0.0)
+        assert np.max(np.abs(rr[lo:hi] - res)) <= 1e3 * f * (np.max(np.abs(ys[lo:hi])) + 1e-300)
+        checked += 1
+    assert checked > 120
+    assert {int(m) for m in b["degree"]} == set(range(1, 9))
+
+
 def test_table5_sum_of_squared_errors(L):
     # Section III, Table I data, m = 3: the GPU's SSE of its own fit equals the
     # exact least-squares minimum and does not exceed the paper's printed value.
