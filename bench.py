@@ -351,7 +351,7 @@ def run_single_large(args, dist: Dist):
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6800 GB/s"}
     cpu = None
-    if dist.rank == 0 and not args.no_cpu_baseline:
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_single(d["x"], d["y"], m, args.cpu_seconds)
     value = dist.world * n * args.steps / (ms_max / 1e3)
     line = {
@@ -548,7 +548,7 @@ def run_ragged_batch(args, dist: Dist):
                "d2h_bytes_per_step": 8 * (m_max + 1) * S, "ms_per_step": e_ms}
 
     cpu = None
-    if dist.rank == 0 and not args.no_cpu_baseline:
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         import oracle
         rng = np.random.default_rng(7)
         pick = rng.choice(S, min(S, 3000), replace=False)
@@ -959,7 +959,7 @@ def run_general(args, dist: Dist):
     kname = "gen_kernel_{}<{},F32,{},W={},CHEB={}>".format("f64" if accum == "f64" else "f32", m, accum,
                                                           int(weighted), int(basis == "chebyshev"))
     cpu = None
-    if dist.rank == 0 and not args.no_cpu_baseline:
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_general(d["x"] if (lo, hi) == (-1.0, 1.0) else hx.numpy(), d["y"],
                                    hw.numpy() if weighted else None, m, basis, interval, args.cpu_seconds,
                                    fp32=accum != "f64")
