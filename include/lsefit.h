@@ -447,7 +447,9 @@ size_t lsefit_residuals_workspace_size(const lsefit_plan* plan);
  *  r         device array like y or NULL: per-point residuals (FP32 for
  *            F32/BF16 data, FP64 for F64 data).
  *  sse       device double[num_series]: NaN for a series whose fit failed.
- *  vtr       device double[num_series][m_max+1] or NULL.
+ *  vtr       device double[num_series][m_max+1] or NULL: entries k <= m, NaN
+ *            for a failed fit; entries k > m are 0; a degree outside
+ *            1..m_max gives a row of NaN.
  *  workspace device, >= lsefit_residuals_workspace_size(plan), 256-byte
  *            aligned; no initialization needed.
  */

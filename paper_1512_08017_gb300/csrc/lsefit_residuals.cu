@@ -245,6 +245,16 @@ __device__ __forceinline__ void rs_store(const RsParams& p, int64_t s, int M, co
     }
 }
 
+// A series whose degree is outside 1..8: SSE and the whole V^T r row are NaN.
+__device__ __forceinline__ void rs_store_invalid(const RsParams& p, int64_t s) {
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    p.sse[s] = qnan;
+    if (p.vtr) {
+        const int nc = p.m_max + 1;
+        for (int k = 0; k < nc; ++k) p.vtr[s * nc + k] = qnan;
+    }
+}
+
 template <int DT, int M, bool CHEB>
 __device__ void rs_block_task(const RsParams& p, int t, int4 task, dflt* red, double* red64, double* tot,
                               int* s_last) {
@@ -347,7 +357,7 @@ __global__ void __launch_bounds__(kRsBlock) residuals_kernel(RsParams p) {
             case 7: rs_block_task<DT, 7, CHEB>(p, t, task, red, red64, tot, &s_last); break;
             case 8: rs_block_task<DT, 8, CHEB>(p, t, task, red, red64, tot, &s_last); break;
             default:
-                if (tid == 0 && task.y == 0) p.sse[task.x] = __longlong_as_double(0x7ff8000000000000ll);
+                if (tid == 0 && task.y == 0) rs_store_invalid(p, task.x);
                 break;
         }
         __syncthreads();
@@ -368,7 +378,7 @@ __global__ void __launch_bounds__(kRsBlock) residuals_kernel(RsParams p) {
             case 7: rs_warp_task<DT, 7, CHEB>(p, s); break;
             case 8: rs_warp_task<DT, 8, CHEB>(p, s); break;
             default:
-                if (lane == 0) p.sse[s] = __longlong_as_double(0x7ff8000000000000ll);
+                if (lane == 0) rs_store_invalid(p, s);
                 break;
         }
     }

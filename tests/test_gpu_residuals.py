@@ -108,6 +108,57 @@ def test_residuals_chebyshev_basis(L, dtype, accum, tuning):
     assert {int(m) for m in b["degree"]} == set(range(1, 9))
 
 
+@pytest.mark.parametrize("basis", ["monomial", "chebyshev"])
+def test_residuals_edge_series(L, basis):
+    """Empty, too short, exactly interpolated, singular, non-finite, bad-interval
+    and out-of-range-degree series: NaN SSE and V^T r for every failed fit (a
+    whole NaN row for a degree outside 1..m_max), the oracle's values elsewhere."""
+    rng = np.random.default_rng(93)
+    lengths = np.array([0, 1, 2, 3, 6, 50, 5000, 70000, 0, 20, 20, 20, 33, 9000])
+    b = synth.ragged_batch(lengths=lengths, seed=93, a_range=(-5.0, 5.0), w_range=(1.0, 8.0))
+    b["degree"][:] = rng.integers(1, 6, lengths.size).astype(np.int32)
+    b["degree"][3] = 3      # n = 3 < m + 1
+    b["degree"][4] = 5      # n = m + 1: exact interpolation, SSE ~ 0
+    b["degree"][12] = 0     # not fitted
+    off = b["offsets"]
+    b["x"][off[9]: off[10]] = b["x"][off[9]]           # all-equal x: singular
+    b["y"][off[10] + 4] = np.nan                      # non-finite
+    b["interval"][11] = (2.0, 2.0)                    # bad interval
+    x = torch.from_numpy(b["x"]).cuda()
+    y = torch.from_numpy(b["y"]).cuda()
+    for tuning in (None, {"warp_max_len": 8, "chunk_len": 1024}):
+        plan = L.BatchPlan(b["offsets"], 5, tuning=tuning, degree=b["degree"])
+        fwd = L.fit_batched(x, y, b["offsets"], b["degree"], b["interval"], m_max=5, accum="comp", plan=plan,
+                            basis=basis)
+        out = L.residuals_batched(x, y, b["offsets"], b["degree"], fwd)
+        st = L.status_names(fwd["status"])
+        sse = out["sse"].cpu().numpy()
+        vtr = out["vtr"].cpu().numpy()
+        assert st[12] == "invalid_arg" and np.isnan(sse[12]) and np.all(np.isnan(vtr[12]))
+        good = 0
+        for s in range(lengths.size):
+            m = int(b["degree"][s])
+            if s == 12:
+                continue
+            if st[s] != "ok":
+                assert np.isnan(sse[s]) and np.all(np.isnan(vtr[s, : m + 1])) and np.all(vtr[s, m + 1:] == 0), s
+                continue
+            lo, hi = int(off[s]), int(off[s + 1])
+            r = oracle.fit_general_interval(b["x"][lo:hi], b["y"][lo:hi], m, *b["interval"][s], fp32=True,
+                                            basis=basis)
+            if r["status"] != "ok":
+                continue  # the 6-point degree-5 monomial system sits at the FP32 singularity threshold
+            sse_ref, _, _ = oracle.residuals_general(b["x"][lo:hi], b["y"][lo:hi], r["Xb"], basis,
+                                                     cs=(r["c"], r["s"]))
+            ymax = float(np.max(np.abs(b["y"][lo:hi])))
+            # absolute slack for the exactly interpolated series (SSE ~ 0): FP32 residuals
+            assert abs(sse[s] - sse_ref) <= 1e-4 * sse_ref + (hi - lo) * (1e-4 * ymax) ** 2, (s, sse[s], sse_ref)
+            good += 1
+        assert st[0] == "n_too_small" and st[3] == "n_too_small" and st[8] == "n_too_small"
+        assert st[9] == "singular" and st[10] == "nonfinite" and st[11] == "bad_interval"
+        assert good >= 5
+
+
 def test_table5_sum_of_squared_errors(L):
     # Section III, Table I data, m = 3: the GPU's SSE of its own fit equals the
     # exact least-squares minimum and does not exceed the paper's printed value.
