@@ -57,7 +57,7 @@ def parse_args(argv=None):
                    help="batched schedule as JSON (e.g. '{\"warp_max_len\": 1048576}'); default: autotune")
     p.add_argument("--accum", default="comp", choices=["comp", "naive", "f64"])
     p.add_argument("--basis", default="monomial", choices=["monomial", "chebyshev"],
-                   help="basis of the ragged_batch fit (chebyshev: no residual pass or plain comparison)")
+                   help="basis of the ragged_batch fit (chebyshev: no plain per-series comparison)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=10.0,

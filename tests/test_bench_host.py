@@ -1,0 +1,74 @@
+"""Host logic of bench.py (no GPU): the traffic record tied to the CUDA sources
+it was captured on, the peaks file and its fallback, the host description, and
+the defaults the timing contract asks for."""
+import json
+import os
+import shutil
+
+import bench
+
+
+def _fake_root(tmp_path, with_csrc=True):
+    root = tmp_path / "root"
+    (root / "profiles").mkdir(parents=True)
+    if with_csrc:
+        shutil.copytree(os.path.join(bench.ROOT, "paper_1512_08017_gb300", "csrc"),
+                        root / "paper_1512_08017_gb300" / "csrc")
+    return root
+
+
+def test_source_digest_follows_the_kernel_sources(tmp_path, monkeypatch):
+    root = _fake_root(tmp_path)
+    real = bench.source_digest()
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.source_digest() == real
+    f = root / "paper_1512_08017_gb300" / "csrc" / "lsefit_device.cuh"
+    f.write_text(f.read_text() + "\n// edited\n")
+    assert bench.source_digest() != real
+
+
+def test_recorded_traffic_only_for_the_current_sources(tmp_path, monkeypatch):
+    root = _fake_root(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    dig = bench.source_digest()
+    rec = {"k_now": {"source_digest": dig, "dram_bytes_per_launch": 123.0},
+           "k_old": {"source_digest": "0" * 16, "dram_bytes_per_launch": 456.0}}
+    (root / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    assert bench.recorded_traffic("k_now") == 123.0
+    assert bench.recorded_traffic("k_old") is None      # captured on other sources: null
+    assert bench.recorded_traffic("missing") is None
+    (root / "profiles" / "traffic.json").write_text("not json")
+    assert bench.recorded_traffic("k_now") is None
+
+
+def test_committed_traffic_records_are_well_formed():
+    with open(os.path.join(bench.ROOT, "profiles", "traffic.json")) as f:
+        rec = json.load(f)
+    for key in ("powersums_f32_comp_m3", "batched_f32_comp", "residuals_f32", "diff_fwd_bwd",
+                "general_weighted", "general_chebyshev"):
+        v = rec[key]
+        assert len(v["source_digest"]) == 16 and v["dram_bytes_per_launch"] > 0
+        assert abs(v["dram_bytes_per_launch"] - v["captured_bytes"] * v["scale"]) <= 1e-6 * v["captured_bytes"] * v["scale"]
+        assert v["kernels"] and v["note"]
+
+
+def test_measured_peaks_and_fallback(tmp_path, monkeypatch):
+    root = _fake_root(tmp_path, with_csrc=False)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    peaks, kind = bench.measured_peaks()
+    assert kind == "fallback" and peaks["hbm_gbs"] == 6800.0
+    (root / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 7000.0, "bf16_tflops": 2000.0}))
+    peaks, kind = bench.measured_peaks()
+    assert kind == "measured" and peaks["hbm_gbs"] == 7000.0
+
+
+def test_host_info():
+    h = bench.host_info()
+    assert h["nproc"] >= 1 and h["machine"]
+
+
+def test_contract_defaults():
+    a = bench.parse_args([])
+    assert a.gpus == 1 and a.impl == "lsefit" and a.workload == "single_large"
+    assert a.warmup >= 3 and a.steps >= 1
+    assert a.n == 1 << 28
