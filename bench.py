@@ -172,14 +172,38 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def source_digest() -> str:
-    """Hash of the CUDA sources (ties a recorded ncu traffic figure to the kernel it came from)."""
-    h = hashlib.sha256()
+# Sources each recorded kernel is built from (traffic.json key prefix -> files
+# of paper_1512_08017_gb300/csrc besides the shared ones); other keys hash
+# every source file.
+_SHARED_SOURCES = ("lsefit_device.cuh", "lsefit_host.h", "lsefit_api.cu")
+_KERNEL_SOURCES = {
+    "powersums": ("lsefit_powersums.cu",),
+    "batched": ("lsefit_batched.cuh", "lsefit_batched.cu", "lsefit_batched_*.cu"),
+    "residuals": ("lsefit_residuals.cu",),
+    "general": ("lsefit_general.cuh", "lsefit_general.cu", "lsefit_general_*.cu"),
+    "diff": ("lsefit_batched.cuh", "lsefit_batched.cu", "lsefit_batched_*.cu", "lsefit_backward.cu"),
+}
+
+
+def source_digest(kernel_key: str | None = None) -> str:
+    """Hash of the CUDA sources a kernel is built from, plus the C header (ties a
+    recorded ncu traffic figure to the code it was captured on).  Without a key,
+    or for an unknown one, every source file."""
+    import fnmatch
     csrc = os.path.join(ROOT, "paper_1512_08017_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    names = sorted(os.listdir(csrc))
+    prefix = (kernel_key or "").split("_")[0]
+    if prefix in _KERNEL_SOURCES:
+        pats = _SHARED_SOURCES + _KERNEL_SOURCES[prefix]
+        names = [n for n in names if any(fnmatch.fnmatch(n, p) for p in pats)]
+    h = hashlib.sha256()
+    for name in names:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
+    with open(os.path.join(ROOT, "include", "lsefit.h"), "rb") as f:
+        h.update(b"lsefit.h")
+        h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -191,7 +215,7 @@ def recorded_traffic(kernel_key: str):
             rec = json.load(f).get(kernel_key)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("source_digest") != source_digest():
+    if not rec or rec.get("source_digest") != source_digest(kernel_key):
         return None
     return rec.get("dram_bytes_per_launch")
 

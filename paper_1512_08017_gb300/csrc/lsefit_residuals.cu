@@ -347,7 +347,8 @@ __global__ void __launch_bounds__(kRsBlock) residuals_kernel(RsParams p) {
         if (t >= p.n_block_tasks) break;
         const int4 task = p.block_tasks[t];
         const int m = p.degree[task.x];
-        switch (m) {
+        // a degree above m_max has no coefficient row of its length: invalid
+        switch (m <= p.m_max ? m : 0) {
             case 1: rs_block_task<DT, 1, CHEB>(p, t, task, red, red64, tot, &s_last); break;
             case 2: rs_block_task<DT, 2, CHEB>(p, t, task, red, red64, tot, &s_last); break;
             case 3: rs_block_task<DT, 3, CHEB>(p, t, task, red, red64, tot, &s_last); break;
@@ -368,7 +369,8 @@ __global__ void __launch_bounds__(kRsBlock) residuals_kernel(RsParams p) {
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= p.n_warp_tasks) break;
         const int64_t s = p.warp_tasks[t].x;
-        switch (p.degree[s]) {
+        const int m = p.degree[s];
+        switch (m <= p.m_max ? m : 0) {
             case 1: rs_warp_task<DT, 1, CHEB>(p, s); break;
             case 2: rs_warp_task<DT, 2, CHEB>(p, s); break;
             case 3: rs_warp_task<DT, 3, CHEB>(p, s); break;

@@ -19,18 +19,32 @@ def _fake_root(tmp_path, with_csrc=True):
 
 def test_source_digest_follows_the_kernel_sources(tmp_path, monkeypatch):
     root = _fake_root(tmp_path)
-    real = bench.source_digest()
+    (root / "include").mkdir()
+    shutil.copy(os.path.join(bench.ROOT, "include", "lsefit.h"), root / "include" / "lsefit.h")
+    keys = ("powersums_f32_comp_m3", "residuals_f32", "batched_f32_comp", "general_weighted", "diff_fwd_bwd")
+    real = {k: bench.source_digest(k) for k in keys + (None,)}
     monkeypatch.setattr(bench, "ROOT", str(root))
-    assert bench.source_digest() == real
-    f = root / "paper_1512_08017_gb300" / "csrc" / "lsefit_device.cuh"
+    assert {k: bench.source_digest(k) for k in keys + (None,)} == real
+    # a kernel's own file changes its digest only
+    f = root / "paper_1512_08017_gb300" / "csrc" / "lsefit_residuals.cu"
     f.write_text(f.read_text() + "\n// edited\n")
-    assert bench.source_digest() != real
+    assert bench.source_digest("residuals_f32") != real["residuals_f32"]
+    assert bench.source_digest(None) != real[None]
+    for k in ("powersums_f32_comp_m3", "batched_f32_comp", "general_weighted", "diff_fwd_bwd"):
+        assert bench.source_digest(k) == real[k], k
+    # a shared header changes every digest
+    g = root / "paper_1512_08017_gb300" / "csrc" / "lsefit_device.cuh"
+    g.write_text(g.read_text() + "\n// edited\n")
+    for k in keys:
+        assert bench.source_digest(k) != real[k], k
 
 
 def test_recorded_traffic_only_for_the_current_sources(tmp_path, monkeypatch):
     root = _fake_root(tmp_path)
+    (root / "include").mkdir()
+    shutil.copy(os.path.join(bench.ROOT, "include", "lsefit.h"), root / "include" / "lsefit.h")
     monkeypatch.setattr(bench, "ROOT", str(root))
-    dig = bench.source_digest()
+    dig = bench.source_digest("k_now")
     rec = {"k_now": {"source_digest": dig, "dram_bytes_per_launch": 123.0},
            "k_old": {"source_digest": "0" * 16, "dram_bytes_per_launch": 456.0}}
     (root / "profiles" / "traffic.json").write_text(json.dumps(rec))

@@ -111,15 +111,18 @@ def test_residuals_chebyshev_basis(L, dtype, accum, tuning):
 @pytest.mark.parametrize("basis", ["monomial", "chebyshev"])
 def test_residuals_edge_series(L, basis):
     """Empty, too short, exactly interpolated, singular, non-finite, bad-interval
-    and out-of-range-degree series: NaN SSE and V^T r for every failed fit (a
-    whole NaN row for a degree outside 1..m_max), the oracle's values elsewhere."""
+    and out-of-range-degree series (0, and 6 and 9 above m_max = 5): NaN SSE and
+    V^T r for every failed fit (a whole NaN row for a degree outside 1..m_max),
+    the oracle's values elsewhere."""
     rng = np.random.default_rng(93)
-    lengths = np.array([0, 1, 2, 3, 6, 50, 5000, 70000, 0, 20, 20, 20, 33, 9000])
+    lengths = np.array([0, 1, 2, 3, 6, 50, 5000, 70000, 0, 20, 20, 20, 33, 9000, 100, 200])
     b = synth.ragged_batch(lengths=lengths, seed=93, a_range=(-5.0, 5.0), w_range=(1.0, 8.0))
     b["degree"][:] = rng.integers(1, 6, lengths.size).astype(np.int32)
     b["degree"][3] = 3      # n = 3 < m + 1
     b["degree"][4] = 5      # n = m + 1: exact interpolation, SSE ~ 0
     b["degree"][12] = 0     # not fitted
+    b["degree"][14] = 6     # above m_max = 5
+    b["degree"][15] = 9     # above every kernel's degree
     off = b["offsets"]
     b["x"][off[9]: off[10]] = b["x"][off[9]]           # all-equal x: singular
     b["y"][off[10] + 4] = np.nan                      # non-finite
@@ -134,11 +137,12 @@ def test_residuals_edge_series(L, basis):
         st = L.status_names(fwd["status"])
         sse = out["sse"].cpu().numpy()
         vtr = out["vtr"].cpu().numpy()
-        assert st[12] == "invalid_arg" and np.isnan(sse[12]) and np.all(np.isnan(vtr[12]))
+        for s in (12, 14, 15):
+            assert st[s] == "invalid_arg" and np.isnan(sse[s]) and np.all(np.isnan(vtr[s])), s
         good = 0
         for s in range(lengths.size):
             m = int(b["degree"][s])
-            if s == 12:
+            if s in (12, 14, 15):
                 continue
             if st[s] != "ok":
                 assert np.isnan(sse[s]) and np.all(np.isnan(vtr[s, : m + 1])) and np.all(vtr[s, m + 1:] == 0), s
