@@ -53,6 +53,10 @@ def parse_args(argv=None):
     p.add_argument("--n", type=int, default=1 << 28, help="points of the single_large series")
     p.add_argument("--series", type=int, default=65536, help="series of the ragged_batch workload")
     p.add_argument("--no-plain", action="store_true", help="skip the plain per-series comparison")
+    p.add_argument("--coef-sample", type=int, default=2048,
+                   help="series of a batch checked against the oracle after the timed region")
+    p.add_argument("--no-sub", action="store_true",
+                   help="default workload: skip the ragged and differentiable sub-records")
     p.add_argument("--tuning", default=None,
                    help="batched schedule as JSON (e.g. '{\"warp_max_len\": 1048576}'); default: autotune")
     p.add_argument("--accum", default="comp", choices=["comp", "naive", "f64"])
@@ -60,7 +64,7 @@ def parse_args(argv=None):
                    help="basis of the ragged_batch fit (chebyshev: no plain per-series comparison)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-seconds", type=float, default=10.0,
+    p.add_argument("--cpu-seconds", type=float, default=6.0,
                    help="target CPU time of the oracle baseline sample")
     return p.parse_args(argv)
 
@@ -242,6 +246,11 @@ def host_info() -> dict:
 
 
 def cpu_baseline_single(x: np.ndarray, y: np.ndarray, m: int, target_s: float):
+    """The oracle on the host cores, two ways: the sequential oracle itself (one
+    thread, on the first 2^24 points) and its all-core variant (per-thread power
+    sums over fixed equal point ranges, added in thread order, on every point);
+    both then solve degrees m..1 by the oracle's elimination.  The all-core
+    figure is the line's value."""
     import oracle
     n = x.size
     sample = min(n, 1 << 24)
@@ -252,15 +261,154 @@ def cpu_baseline_single(x: np.ndarray, y: np.ndarray, m: int, target_s: float):
     while reps < 3 or t_total < target_s:
         t0 = time.perf_counter()
         out = oracle.fit(xs, ys, m)
+        for k in range(m - 1, 0, -1):
+            oracle.solve(out["S"][: 2 * k + 1], out["T"][: k + 1], k)
         t_total += time.perf_counter() - t0
         reps += 1
         if reps >= 1000:
             break
     assert out["status"] == "ok"
-    return {"value": sample * reps / t_total, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
-            "sample": f"first {sample} points of the series, degree {m} fit "
-                      f"(FP64 sums + Gaussian elimination, sequential C), {reps} repetitions, "
-                      f"{t_total:.1f} s"}
+    single = {"value": sample * reps / t_total, "unit": UNIT, "cores": 1, "kind": "oracle",
+              "sample": f"first {sample} points of the series, degrees {m}..1 (FP64 sums + Gaussian elimination, "
+                        f"sequential C), {reps} repetitions, {t_total:.1f} s"}
+    del xs, ys
+    threads = oracle.host_threads()
+    x64 = x.astype(np.float64)
+    y64 = y.astype(np.float64)
+    reps, t_total = 0, 0.0
+    while reps < 2 or t_total < max(1.0, target_s / 3):
+        t0 = time.perf_counter()
+        out = oracle.fit_threads(x64, y64, m, threads=threads)
+        for k in range(m - 1, 0, -1):
+            oracle.solve(out["S"][: 2 * k + 1], out["T"][: k + 1], k)
+        t_total += time.perf_counter() - t0
+        reps += 1
+        if reps >= 200:
+            break
+    assert out["status"] == "ok"
+    return {"value": n * reps / t_total, "unit": UNIT, "cores": threads, "kind": "oracle", "host": host_info(),
+            "sample": f"all {n} points, degrees {m}..1: FP64 power sums on {threads} threads (fixed equal point "
+                      f"ranges, the sequential oracle per range, added in thread order) + the oracle's Gaussian "
+                      f"elimination; {reps} repetitions, {t_total:.1f} s",
+            "single_thread": single}
+
+
+def rel_err(a, b) -> float:
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def backward_err(S, T, m, Xt) -> float:
+    """Normwise backward error of Xt in the oracle's normal equations A Xt = B
+    (A[j][k] = S[j+k], B = T): the smallest relative change of A and B that makes
+    Xt exact; it does not grow with cond(A)."""
+    A = np.array([[S[j + k] for k in range(m + 1)] for j in range(m + 1)], dtype=np.float64)
+    B = np.asarray(T[: m + 1], dtype=np.float64)
+    Xt = np.asarray(Xt, dtype=np.float64)
+    return float(np.linalg.norm(A @ Xt - B) / (np.linalg.norm(A, 2) * np.linalg.norm(Xt) + np.linalg.norm(B)))
+
+
+def coef_err_single(x: np.ndarray, y: np.ndarray, out: dict, m: int, m_lo: int = 1) -> dict:
+    """Error of the timed single-series result (every degree m_lo..m, no interval)
+    against the sequential FP64 oracle on all the stored points."""
+    import oracle
+    t0 = time.perf_counter()
+    ref = oracle.fit(x.astype(np.float64), y.astype(np.float64), m, eps=oracle.EPS32)
+    X = out["X"].cpu().numpy()
+    Xt = out["Xt"].cpu().numpy()
+    per = []
+    for r, d in enumerate(range(m_lo, m + 1)):
+        st, Xo = oracle.solve(ref["S"][: 2 * d + 1], ref["T"][: d + 1], d, eps=oracle.EPS32)
+        per.append({"m": d, "status": st, "X": rel_err(X[r, : d + 1], Xo), "Xt": rel_err(Xt[r, : d + 1], Xo),
+                    "backward": backward_err(ref["S"], ref["T"], d, Xt[r, : d + 1])})
+    return {"max_rel_X": max(p["X"] for p in per), "max_rel_Xt": max(p["Xt"] for p in per),
+            "max_backward": max(p["backward"] for p in per), "per_degree": per,
+            "tolerance": 1e-5, "oracle": f"sequential FP64 oracle on all {x.size} stored points",
+            "oracle_s": time.perf_counter() - t0}
+
+
+# ---------------------------------------------------------------------------
+# host link: rate of one large pinned copy and where the buffers sit
+# ---------------------------------------------------------------------------
+_SYS_MOVE_PAGES = {"x86_64": 279, "aarch64": 239}
+
+
+def page_node(addr: int):
+    """NUMA node of the page holding host address addr (move_pages(2) query,
+    no move), or None where the kernel does not say."""
+    import ctypes
+    import platform
+    nr = _SYS_MOVE_PAGES.get(platform.machine())
+    if nr is None:
+        return None
+    try:
+        libc = ctypes.CDLL(None, use_errno=True)
+        pages = (ctypes.c_void_p * 1)(addr & ~4095)
+        status = (ctypes.c_int * 1)(-1)
+        rc = libc.syscall(ctypes.c_long(nr), ctypes.c_int(0), ctypes.c_ulong(1), pages, None, status,
+                          ctypes.c_int(0))
+    except (OSError, AttributeError):
+        return None
+    return int(status[0]) if rc == 0 and status[0] >= 0 else None
+
+
+def gpu_numa_node(device_index: int):
+    """NUMA node the GPU's PCI function reports (sysfs), or None."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", str(device_index), "--query-gpu=pci.bus_id",
+                              "--format=csv,noheader"], capture_output=True, text=True, timeout=20).stdout.strip()
+    except (OSError, subprocess.TimeoutExpired):
+        return None
+    if not out:
+        return None
+    dom, rest = out.split(":", 1)
+    for name in (f"{int(dom, 16):04x}:{rest}".lower(), out.lower()):
+        try:
+            with open(f"/sys/bus/pci/devices/{name}/numa_node") as f:
+                return int(f.read().strip())
+        except (OSError, ValueError):
+            continue
+    return None
+
+
+def numa_nodes_with_cpus():
+    base = "/sys/devices/system/node"
+    nodes = {}
+    try:
+        for name in sorted(os.listdir(base)):
+            if name.startswith("node") and name[4:].isdigit():
+                with open(os.path.join(base, name, "cpulist")) as f:
+                    nodes[int(name[4:])] = f.read().strip()
+    except OSError:
+        pass
+    return nodes
+
+
+def link_probe(host: "torch.Tensor", dev: "torch.Tensor", stream, reps: int = 3) -> dict:
+    """Best H2D and D2H GB/s of one copy of the whole pinned buffer, and where
+    the buffer and the GPU sit."""
+    import torch
+    h2d = d2h = 0.0
+    nbytes = host.numel() * host.element_size()
+    for _ in range(reps):
+        for direction in ("h2d", "d2h"):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if direction == "h2d":
+                dev.copy_(host, non_blocking=True)
+            else:
+                host.copy_(dev, non_blocking=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            gbs = nbytes / (a.elapsed_time(b) / 1e3) / 1e9
+            if direction == "h2d":
+                h2d = max(h2d, gbs)
+            else:
+                d2h = max(d2h, gbs)
+    return {"h2d_gbs": h2d, "d2h_gbs": d2h, "bytes": nbytes, "pinned_node": page_node(host.data_ptr()),
+            "gpu_node": gpu_numa_node(torch.cuda.current_device()), "nodes_with_cpus": numa_nodes_with_cpus()}
 
 
 # ---------------------------------------------------------------------------
@@ -364,7 +512,8 @@ def run_single_large(args, dist: Dist):
         e2e = {"value": best["value"], "unit": UNIT,
                "h2d_bytes_per_step": 2 * n * 4, "d2h_bytes_per_step": 4 * 8,
                "steps": e_steps, "ms_per_step": best["ms_per_step"],
-               "mode": "mapped" if best is mapped_mode else "copy", "copy": copy_mode, "mapped": mapped_mode}
+               "mode": "mapped" if best is mapped_mode else "copy", "copy": copy_mode, "mapped": mapped_mode,
+               "link": link_probe(hx, x, stream)}
 
     peaks, peak_kind = measured_peaks()
     algo_bytes = 8 * n
@@ -374,6 +523,8 @@ def run_single_large(args, dist: Dist):
                 "kernel": "ps_kernel_f32<3,F32,comp> (fused solves of degrees 1-3)", "kernel_ms": kern_ms_max,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6800 GB/s"}
+    # error of the timed result against the oracle on every stored point (after the timed region)
+    coef = coef_err_single(d["x"], d["y"], out, m) if dist.rank == 0 else None
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_single(d["x"], d["y"], m, args.cpu_seconds)
@@ -387,7 +538,7 @@ def run_single_large(args, dist: Dist):
                    "n": n, "m": [3, 2, 1], "accum": args.accum, "solve": "fp64 GE, partial pivoting",
                    "l2": "inputs (2 GiB) larger than L2; no flush", "parallelism": f"replicas x{dist.world}"},
         "hbm_gbs": algo_bytes / (ms_max / args.steps / 1e3) / 1e9,
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+        "roofline": roofline, "coef_err": coef, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
         "gpu_launches": args.steps,
     }
     return line
@@ -444,6 +595,51 @@ def _roofline_fp64(flops, kern_ms, kernel):
     return {"bound": "fp64", "achieved": achieved, "peak": 1250.0, "unit": "GFLOP/s", "frac": achieved / 1250.0,
             "traffic": None, "kernel": kernel, "kernel_ms": kern_ms,
             "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 figure)"}
+
+
+def coef_err_batched(b: dict, res: dict, series, basis: str = "monomial", accum: str = "comp") -> dict:
+    """Error of a batched result on the given series against the sequential
+    oracle (same stored points, same map): statuses, the normwise error of the
+    mapped-basis coefficients where the system determines them to 1e-3 or
+    better (cond(A) 2^-24 4m <= 1e-3), and the backward error everywhere."""
+    import oracle
+    t0 = time.perf_counter()
+    Xt = res["Xt"].cpu().numpy()
+    st = res["status"].cpu().numpy()
+    names = {0: "ok", 2: "n_too_small", 3: "singular", 4: "nonfinite", 5: "bad_interval"}
+    x64 = b["x"]
+    y64 = b["y"]
+    fwd_max, bwd_max, mismatched, undetermined, checked = 0.0, 0.0, 0, 0, 0
+    for s_ in series:
+        lo, hi = int(b["offsets"][s_]), int(b["offsets"][s_ + 1])
+        m = int(b["degree"][s_])
+        xs = x64[lo:hi].astype(np.float64)
+        ys = y64[lo:hi].astype(np.float64)
+        if basis == "monomial":
+            r = oracle.fit_interval(xs, ys, m, *b["interval"][s_], fp32=accum != "f64")
+            ref, A, B = r["Xt"], (None if r["S"] is None else
+                                  np.array([[r["S"][j + k] for k in range(m + 1)] for j in range(m + 1)])), r["T"]
+        else:
+            r = oracle.fit_general_interval(xs, ys, m, *b["interval"][s_], fp32=accum != "f64", basis="chebyshev")
+            ref, A, B = r["Xb"], r["G"], r["b"]
+        if names.get(int(st[s_]), "other") != r["status"]:
+            mismatched += 1
+            continue
+        if r["status"] != "ok":
+            continue
+        checked += 1
+        got = Xt[s_, : m + 1]
+        eta = float(np.linalg.norm(A @ got - B) / (np.linalg.norm(A, 2) * np.linalg.norm(got) + np.linalg.norm(B)))
+        bwd_max = max(bwd_max, eta)
+        cond = float(np.linalg.cond(A))
+        eps = 2.0 ** -53 if accum == "f64" else 2.0 ** -24
+        if cond * eps * 4 * m <= 1e-3:
+            fwd_max = max(fwd_max, rel_err(got, ref))
+        else:
+            undetermined += 1
+    return {"series_checked": checked, "status_mismatches": mismatched, "max_rel_Xt": fwd_max,
+            "max_backward": bwd_max, "undetermined_reported": undetermined,
+            "oracle": f"sequential FP64 oracle per series ({basis} basis)", "oracle_s": time.perf_counter() - t0}
 
 
 # ---------------------------------------------------------------------------
@@ -543,6 +739,17 @@ def run_ragged_batch(args, dist: Dist):
     fwd_full = L.fit_batched(x, y, off, deg, iv, m_max=m_max, accum=args.accum, plan=plan, basis=args.basis)
     res_out = L.residuals_batched(x, y, off, deg, fwd_full)
     torch.cuda.synchronize()
+    coef = None
+    if dist.rank == 0:
+        # the timed graph's coefficients are these, bit for bit; a sample of series
+        # (and the longest and shortest) against the oracle
+        same = bool(torch.equal(torch.nan_to_num(fwd_full["X"]), torch.nan_to_num(out["X"])))
+        rng = np.random.default_rng(11)
+        lens = np.diff(b["offsets"])
+        pick = sorted(set(rng.choice(S, min(S, args.coef_sample), replace=False).tolist())
+                      | {int(np.argmax(lens)), int(np.argmin(lens))})
+        coef = coef_err_batched(b, fwd_full, pick, args.basis, args.accum)
+        coef["timed_result_identical"] = same
     assert bool(torch.isfinite(res_out["sse"]).all())
     rper, _ = _event_steps(lambda: L.residuals_batched(x, y, off, deg, fwd_full), args.steps, stream)
     r_ms = dist.max(statistics.mean(rper))
@@ -604,7 +811,7 @@ def run_ragged_batch(args, dist: Dist):
                               "batched_f32_comp" if args.basis == "monomial" else "batched_f32_comp_chebyshev"),
         "plain_per_series": plain,
         "speedup_vs_plain": (plain["ms_per_step"] / (ms / args.steps)) if plain else None,
-        "residuals": residuals,
+        "coef_err": coef, "residuals": residuals,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": 2 * args.steps,
     }
 
@@ -669,11 +876,43 @@ def run_diff_batch(args, dist: Dist):
     dist.barrier()
     torch.cuda.synchronize()
     perf, totf = _event_steps(gf.replay, args.steps, stream)
+    dist.barrier()
+    clk_f = clocks.stop()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
     perb, totb = _event_steps(gb.replay, args.steps, stream)
     dist.barrier()
     clk = clocks.stop()
     msf = dist.max(totf) / args.steps
     msb = dist.max(totb) / args.steps
+    # errors of the timed results against the oracle: forward coefficients of a
+    # sample of series, gradients of a few (the oracle's adjoint of its own fit)
+    coef = None
+    if dist.rank == 0:
+        import oracle
+        t0 = time.perf_counter()
+        X = fwd_out["X"].cpu().numpy()
+        Xt_all = fwd_out["Xt"].cpu().numpy()
+        dxh = dx.cpu().numpy()
+        dyh = dy.cpu().numpy()
+        rng = np.random.default_rng(12)
+        pick = sorted(rng.choice(S, min(S, 64), replace=False).tolist())
+        fmax = bmax = gmax = 0.0
+        for i, s_ in enumerate(pick):
+            xs = d["x"][s_].astype(np.float64)
+            ys = d["y"][s_].astype(np.float64)
+            r = oracle.fit_interval(xs, ys, m, -1.0, 1.0, fp32=True)
+            assert r["status"] == "ok"
+            fmax = max(fmax, rel_err(Xt_all[s_], r["Xt"]), rel_err(X[s_], r["X"]))
+            bmax = max(bmax, backward_err(r["S"], r["T"], m, Xt_all[s_]))
+            if i < 8:
+                st, odx, ody = oracle.backward(xs, ys, m, (r["c"], r["s"]), r["S"], r["Xt"], 2.0 * d["w"][s_] * r["X"])
+                gmax = max(gmax, rel_err(dxh[s_ * n:(s_ + 1) * n], odx), rel_err(dyh[s_ * n:(s_ + 1) * n], ody))
+        coef = {"series_checked": len(pick), "max_rel_Xt_X": fmax, "max_backward": bmax,
+                "gradients_checked": min(8, len(pick)), "max_rel_dx_dy": gmax, "tolerance": {"X": 1e-5, "dx_dy": 1e-4},
+                "oracle": "sequential FP64 oracle: fit and adjoint per series", "oracle_s": time.perf_counter() - t0}
     plain = None
     if not args.no_plain:
         # one single-series forward and one single-series backward launch pair per series
@@ -758,11 +997,13 @@ def run_diff_batch(args, dist: Dist):
                                "L = sum w X^2; forward + backward in one CUDA graph",
                    "series": S, "points": N, "accum": args.accum, "tuning": plan.tuning},
         "fwd": {"value": dist.world * N / (msf / 1e3), "unit": UNIT, "ms_per_step": msf,
-                "hbm_gbs": 8 * N / (msf / 1e3) / 1e9},
+                "hbm_gbs": 8 * N / (msf / 1e3) / 1e9,
+                "roofline": _roofline(8 * N, msf, "batched forward (8 B/point)", "diff_fwd"), "clocks": clk_f},
         "fwd_bwd_hbm_gbs": 24 * N / (msb / 1e3) / 1e9,
         "roofline": _roofline(24 * N, msb, "batched forward + lambda + grad kernels", "diff_fwd_bwd"),
         "plain_per_series": plain,
         "speedup_vs_plain": (plain["ms_per_step"] / msb) if plain else None,
+        "coef_err": coef,
         "cpu_baseline": None, "e2e": e2e, "clocks": clk, "gpu_launches": 6 * args.steps,
     }
 
@@ -789,6 +1030,8 @@ def run_solve(args, dist: Dist):
     ok = fwd["status"] == 0
     stream = torch.cuda.current_stream()
     res = {}
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     for method in ("gauss", "cholesky"):
         X = torch.empty(S, m + 1, dtype=torch.float64, device=dev)
         Xt = torch.empty_like(X)
@@ -802,6 +1045,7 @@ def run_solve(args, dist: Dist):
         torch.cuda.synchronize()
         per, total = _event_steps(step, args.steps, stream)
         res[method] = {"ms": dist.max(statistics.mean(per)), "Xt": Xt.clone(), "status": st.clone()}
+    clk = clocks.stop()
     both = ok & (res["gauss"]["status"] == 0) & (res["cholesky"]["status"] == 0)
     a, c = res["gauss"]["Xt"][both], res["cholesky"]["Xt"][both]
     agree = float(((a - c).norm(dim=1) / a.norm(dim=1)).max().item())
@@ -820,7 +1064,7 @@ def run_solve(args, dist: Dist):
             "data": "synthetic (power sums of the seeded ragged batch fitted at degree 5)",
             "config": {"workload": f"{S} degree-5 normal-equation systems from one batched pass, "
                                    "one system per thread", "series": S, "m": m},
-            "gauss": out["gauss"], "cholesky": out["cholesky"], "max_rel_diff_gauss_cholesky": agree,
+            "gauss": out["gauss"], "cholesky": out["cholesky"], "max_rel_diff_gauss_cholesky": agree, "clocks": clk,
             "roofline": {"bound": "fp64 latency", "achieved": out["gauss"]["gflops"], "peak": 1250.0,
                          "unit": "GFLOP/s", "frac": out["gauss"]["gflops"] / 1250.0, "traffic": None,
                          "peak_source": "nominal FP64 (no measured FP64 figure)"},
@@ -846,9 +1090,15 @@ def run_single_fp64(args, dist: Dist):
     for _ in range(args.warmup):
         g.replay()
     torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
     per, total = _event_steps(g.replay, args.steps, stream)
+    dist.barrier()
+    clk = clocks.stop()
     ms = dist.max(total) / args.steps
-    return {"metric": "fit latency (FP64, degrees 1-3 in one launch)", "value": ms * 1e3, "unit": "us",
+    return {"metric": "fit latency (FP64, degrees 1-3 in one launch)", "clocks": clk, "value": ms * 1e3, "unit": "us",
             "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded)", "points_per_s": n / (ms / 1e3),
@@ -1002,39 +1252,112 @@ def run_general(args, dist: Dist):
 
 
 def run_reference(args, dist: Dist):
-    """The oracle timed on the host cores on the same workload and metric."""
+    """The oracle timed on the host cores on the same workload and metric: each
+    step fits degrees 3, 2, 1 of the whole 2^28-point series, the power sums on
+    all host cores (the sequential oracle per fixed point range, added in thread
+    order), then the oracle's Gaussian elimination.  The sequential oracle alone
+    is timed beside it on the first 2^24 points."""
     if dist.rank != 0:
         return None
     import synth
     import oracle
     m = 3
-    sample = min(args.n, 1 << 24)
-    d = synth.single_large(n=sample, m=m, seed=synth.SEED_SINGLE_LARGE)
-    xs = d["x"].astype(np.float64)
-    ys = d["y"].astype(np.float64)
-    oracle.fit(xs[:1024], ys[:1024], m)
-    for _ in range(args.warmup):
-        oracle.fit(xs, ys, m)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        out = oracle.fit(xs, ys, m)
+    n = args.n
+    d = synth.single_large(n=n, m=m, seed=synth.SEED_SINGLE_LARGE)
+    x64 = d["x"].astype(np.float64)
+    y64 = d["y"].astype(np.float64)
+    threads = oracle.host_threads()
+
+    def step():
+        out = oracle.fit_threads(x64, y64, m, threads=threads)
         for k in (2, 1):
             oracle.solve(out["S"][: 2 * k + 1], out["T"][: k + 1], k)
+        return out
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        out = step()
     dt = time.perf_counter() - t0
-    value = sample * args.steps / dt
+    assert out["status"] == "ok"
+    value = n * args.steps / dt
+    sample = min(n, 1 << 24)
+    t1 = time.perf_counter()
+    reps = 0
+    while reps < 2 or time.perf_counter() - t1 < 3.0:
+        oracle.fit(x64[:sample], y64[:sample], m)
+        reps += 1
+    single = sample * reps / (time.perf_counter() - t1)
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": "single series, n=2^28 FP32 points (2 GiB), degrees 3,2,1 from one pass",
-                       "sample_points_per_step": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
-                             "sample": f"first {sample} points per step of the same series"},
+                       "n": n, "oracle_threads": threads},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "host": host_info(),
+                             "sample": f"all {n} points per step: FP64 power sums on {threads} threads (the "
+                                       f"sequential oracle per fixed point range), the oracle's elimination",
+                             "single_thread": {"value": single, "unit": UNIT, "cores": 1,
+                                               "sample": f"first {sample} points, sequential oracle, {reps} fits"}},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+_SUB_KEYS = ("metric", "value", "unit", "ms_per_step", "config", "hbm_gbs", "roofline", "clocks", "fwd",
+             "fwd_bwd_hbm_gbs", "plain_per_series", "speedup_vs_plain", "coef_err", "residuals", "e2e",
+             "gpu_launches")
+
+
+def run_default(args, dist: Dist):
+    """The contract's line (the 2^28-point single series) with the rest of the
+    metric as sub-records: the 65,536-series ragged batch (forward, CUDA graph,
+    against the plain per-series path) and the differentiable 4,096 x 4,096
+    batch (forward and forward + backward), each with its own roofline, clocks
+    and coefficient error."""
+    import torch
+    line = run_single_large(args, dist)
+    if args.no_sub:
+        return line
+    sub = argparse.Namespace(**vars(args))
+    sub.no_cpu_baseline = True
+    for key, runner in (("ragged", run_ragged_batch), ("diff", run_diff_batch)):
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        rec = runner(sub, dist)
+        line[key] = {k: rec[k] for k in _SUB_KEYS if k in rec}
+    return line
+
+
+def launch_local_ranks(n: int, argv) -> int:
+    """`--gpus N` without a launcher: start N ranks of this script on this node
+    (RANK, LOCAL_RANK, WORLD_SIZE and a free 127.0.0.1 port in each one's
+    environment), wait for all, and return the first non-zero exit code."""
+    import socket
+    with socket.socket() as sock:
+        sock.bind(("127.0.0.1", 0))
+        port = sock.getsockname()[1]
+    procs = []
+    for r in range(n):
+        env = dict(os.environ, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE=str(n), LOCAL_WORLD_SIZE=str(n),
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, os.path.abspath(__file__), *argv], env=env))
+    codes = [p.wait() for p in procs]
+    bad = [c for c in codes if c != 0]
+    return bad[0] if bad else 0
+
+
 def main(argv=None):
+    argv = list(sys.argv[1:] if argv is None else argv)
     args = parse_args(argv)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        if args.impl != "reference":
+            import torch
+            have = torch.cuda.device_count() if torch.cuda.is_available() else 0
+            if have < args.gpus:
+                print(f"bench.py: --gpus {args.gpus} asks for {args.gpus} ranks but this node has {have} GPU(s)",
+                      file=sys.stderr)
+                return 2
+        return launch_local_ranks(args.gpus, argv)
     if args.impl == "reference":
         world = int(os.environ.get("WORLD_SIZE", "1"))
         rank = int(os.environ.get("RANK", "0"))
@@ -1049,7 +1372,7 @@ def main(argv=None):
         return 1
     dist = Dist(args.gpus)
     try:
-        runners = {"single_large": run_single_large, "ragged_batch": run_ragged_batch,
+        runners = {"single_large": run_default, "ragged_batch": run_ragged_batch,
                    "diff_batch": run_diff_batch, "single_fp64": run_single_fp64, "general": run_general,
                    "solve": run_solve}
         line = runners[args.workload](args, dist)

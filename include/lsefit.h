@@ -57,7 +57,7 @@ typedef struct CUstream_st* lsefit_stream_t;
 #define LSEFIT_MAX_DEGREE 8
 /* Highest degree of lsefit_fit_general in the Chebyshev basis with FP64 accumulation. */
 #define LSEFIT_MAX_DEGREE_CHEBYSHEV 16
-#define LSEFIT_ABI_VERSION 2
+#define LSEFIT_ABI_VERSION 3
 
 /* Return and status codes. */
 enum {
@@ -203,8 +203,11 @@ int lsefit_fit(const void* x, const void* y, int64_t n, int dtype, int m, int m_
  *    until the process exits.  A request that would need more returns
  *    LSEFIT_ERR_SCRATCH_LIMIT (it cannot happen with valid degrees).
  *  - The first call on a device looks up the array's device address (with
- *    that device current) and caches it; make that first call before any
- *    stream capture.
+ *    that device current) and caches it with the device's current driver
+ *    context; make that first call before any stream capture.  A call in a
+ *    new context of the device (after cudaDeviceReset, or after another
+ *    library reset the primary context) looks the address up again, so
+ *    its first call there must also precede any capture.
  *  - All calls share the one array.  Calls that overlap on the GPU (on
  *    different streams, or from different threads) race on it; serialise
  *    them.  The call clears the ticket word before its launch; the rest of

@@ -54,7 +54,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["cc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c99",
+    cmd = ["cc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c99", "-pthread",
            "-Wall", "-Werror", _SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
@@ -94,6 +94,8 @@ def _load():
         lib.orc_cheb_to_mono.restype = None
         lib.orc_residuals_general.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, i64, dp, dp]
         lib.orc_residuals_general.restype = ctypes.c_double
+        lib.orc_powersums_threads.argtypes = [dp, dp, i64, ctypes.c_int, dp, ctypes.c_int, dp, dp]
+        lib.orc_powersums_threads.restype = ctypes.c_int
         lib.orc_max_degree.argtypes = []
         lib.orc_max_degree.restype = ctypes.c_int
         _lib = lib
@@ -134,6 +136,41 @@ def powersums(x, y, m: int, cs=None):
     _load().orc_powersums(_ptr(x), _ptr(y), x.size, m, _ptr(mp) if mp is not None else None,
                           _ptr(S), _ptr(T))
     return S, T
+
+
+def host_threads() -> int:
+    """Threads the all-core variant uses by default: the host's online CPUs."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except (AttributeError, OSError):
+        return max(1, os.cpu_count() or 1)
+
+
+def powersums_threads(x, y, m: int, cs=None, threads: int | None = None):
+    """powersums on all host cores, for timing only: fixed equal point ranges,
+    one per thread, each summed by the sequential routine; the per-thread sums
+    added in thread order (one thread: identical to powersums)."""
+    x = _f64(x)
+    y = _f64(y)
+    assert x.shape == y.shape and x.ndim == 1
+    S = np.zeros(2 * m + 1)
+    T = np.zeros(m + 1)
+    mp = _f64(cs) if cs is not None else None
+    nt = host_threads() if threads is None else int(threads)
+    st = _load().orc_powersums_threads(_ptr(x), _ptr(y), x.size, m, _ptr(mp) if mp is not None else None, nt,
+                                       _ptr(S), _ptr(T))
+    if st != 0:
+        raise ValueError(f"orc_powersums_threads: {STATUS_NAMES[st]} (threads={nt})")
+    return S, T
+
+
+def fit_threads(x, y, m: int, cs=None, eps: float = EPS64, threads: int | None = None) -> dict:
+    """The fit of ``fit`` with the power sums taken by powersums_threads (timing
+    the oracle on all host cores); the elimination and the un-map are the same."""
+    S, T = powersums_threads(x, y, m, cs, threads)
+    st, Xt = solve(S, T, m, eps)
+    X = unmap(Xt, cs[0], cs[1]) if (cs is not None and st == "ok") else Xt.copy()
+    return {"status": st, "X": X, "Xt": Xt, "S": S, "T": T}
 
 
 def solve(S, T, m: int, eps: float = EPS64):

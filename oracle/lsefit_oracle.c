@@ -41,13 +41,15 @@
  *     fits and other solution methods open): per-point weights w_i, and the
  *     Chebyshev basis T_k(t) in place of t^k (orc_fit_general).
  *
- * Build: cc -O2 -ffp-contract=off -fPIC -shared lsefit_oracle.c -lm
+ * Build: cc -O2 -ffp-contract=off -fPIC -shared -pthread lsefit_oracle.c -lm
  * (-ffp-contract=off keeps every product and sum a separately rounded IEEE
  * operation on every host, so results do not depend on FMA contraction.)
  */
 #include <float.h>
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 /* Oracle status values (own numbering; the test suite maps them by name). */
@@ -456,4 +458,68 @@ double orc_residuals_general(int m, int basis, const double* Xb, const double* m
         for (int k = 0; k <= m; ++k) vtr[k] += phi[k] * r;
     }
     return sse;
+}
+
+/*
+ * The power sums of orc_powersums on all host cores, for timing the oracle
+ * against the GPU (not a second definition: each thread runs orc_powersums
+ * itself).  Thread t of nthreads takes the fixed point range
+ * [n t / nthreads, n (t+1) / nthreads); the per-thread sums are added in
+ * thread order, so the result depends only on n and nthreads, and with one
+ * thread it is orc_powersums bit for bit.  Returns ORC_OK, or ORC_BAD_ARG for
+ * a thread count outside 1..ORC_MAX_THREADS or a thread that could not start.
+ */
+#define ORC_MAX_THREADS 1024
+
+typedef struct {
+    const double* x;
+    const double* y;
+    int64_t n;
+    int m;
+    const double* map;
+    double S[2 * ORC_MAX_M + 1];
+    double T[ORC_MAX_M + 1];
+} orc_range;
+
+static void* orc_range_main(void* arg)
+{
+    orc_range* r = (orc_range*)arg;
+    orc_powersums(r->x, r->y, r->n, r->m, r->map, r->S, r->T);
+    return NULL;
+}
+
+int orc_powersums_threads(const double* x, const double* y, int64_t n, int m, const double* map,
+                          int nthreads, double* S, double* T)
+{
+    if (nthreads < 1 || nthreads > ORC_MAX_THREADS || m < 0 || m > ORC_MAX_M || n < 0) return ORC_BAD_ARG;
+    orc_range* r = (orc_range*)calloc((size_t)nthreads, sizeof(orc_range));
+    pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
+    int* started = (int*)calloc((size_t)nthreads, sizeof(int));
+    int st = ORC_OK;
+    if (!r || !th || !started) st = ORC_BAD_ARG;
+    for (int t = 0; st == ORC_OK && t < nthreads; ++t) {
+        const int64_t lo = n / nthreads * t + (n % nthreads) * t / nthreads;
+        const int64_t hi = n / nthreads * (t + 1) + (n % nthreads) * (t + 1) / nthreads;
+        r[t].x = x + lo;
+        r[t].y = y + lo;
+        r[t].n = hi - lo;
+        r[t].m = m;
+        r[t].map = map;
+        if (pthread_create(&th[t], NULL, orc_range_main, &r[t]) == 0) started[t] = 1;
+        else st = ORC_BAD_ARG;
+    }
+    for (int t = 0; t < nthreads && started; ++t)
+        if (started[t]) pthread_join(th[t], NULL);
+    if (st == ORC_OK) {
+        for (int k = 0; k <= 2 * m; ++k) S[k] = 0.0;
+        for (int k = 0; k <= m; ++k) T[k] = 0.0;
+        for (int t = 0; t < nthreads; ++t) {
+            for (int k = 0; k <= 2 * m; ++k) S[k] += r[t].S[k];  /* S[0]: the range counts, exact */
+            for (int k = 0; k <= m; ++k) T[k] += r[t].T[k];
+        }
+    }
+    free(r);
+    free(th);
+    free(started);
+    return st;
 }

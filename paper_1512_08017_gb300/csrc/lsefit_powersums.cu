@@ -280,25 +280,52 @@ static_assert(kNoallocScratchBytes >= kAlign + (size_t)kMaxGrid * (3 * LSEFIT_MA
               "allocation-free scratch must hold the partials of the largest degree and grid");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-// Device address of g_noalloc_scratch on the current device.  In host code the
-// symbol names a host-side stand-in, not device memory, so the address is
-// looked up once per device (with that device current) and cached.
+// Device address of g_noalloc_scratch in the current context.  In host code
+// the symbol names a host-side stand-in, not device memory, so the address is
+// looked up (with the device current) and cached.  The cache is keyed by
+// device and by the current driver context: a context that was torn down and
+// created again (cudaDeviceReset, or another library resetting the primary
+// context) holds the array at another address, so a new context makes the
+// next call look the address up again.
+typedef int (*ctx_get_current_t)(void** ctx);  // cuCtxGetCurrent(CUcontext*)
+
+static ctx_get_current_t ctx_get_current() {
+    static ctx_get_current_t fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<ctx_get_current_t>(p);
+        (void)cudaGetLastError();
+    });
+    return fn;
+}
+
 static int noalloc_scratch(void** out) {
     static std::mutex mu;
     static void* addr[256] = {nullptr};
+    static void* ctx_of[256] = {nullptr};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
         (void)cudaGetLastError();
         return LSEFIT_ERR_CUDA;
     }
+    // the symbol lookup also makes the device's primary context current
+    void* ctx = nullptr;
+    ctx_get_current_t get = ctx_get_current();
     std::lock_guard<std::mutex> lock(mu);
-    if (addr[dev] == nullptr) {
+    if (get != nullptr && (get(&ctx) != 0 || ctx == nullptr)) ctx = nullptr;
+    if (addr[dev] == nullptr || ctx == nullptr || ctx != ctx_of[dev]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
             (void)cudaGetLastError();
             return LSEFIT_ERR_CUDA;
         }
+        if (get != nullptr && ctx == nullptr && (get(&ctx) != 0)) ctx = nullptr;
         addr[dev] = p;
+        ctx_of[dev] = ctx;
     }
     *out = addr[dev];
     return LSEFIT_OK;
@@ -317,7 +344,10 @@ extern "C" int lsefit_fit_noalloc(const void* x, const void* y, int64_t n, int d
     const int rc = noalloc_scratch(&ws);
     if (rc != LSEFIT_OK) return rc;
     // the ticket word must start at zero (each call also leaves it zeroed)
-    if (cudaMemsetAsync(ws, 0, kAlign, (cudaStream_t)stream) != cudaSuccess) return LSEFIT_ERR_CUDA;
+    if (cudaMemsetAsync(ws, 0, kAlign, (cudaStream_t)stream) != cudaSuccess) {
+        (void)cudaGetLastError();  // the next call must not see this failure as its own
+        return LSEFIT_ERR_CUDA;
+    }
     return lsefit_fit(x, y, n, dtype, m, m_lo, accum, interval, X, Xt, sums, map, status, ws,
                       kNoallocScratchBytes, stream);
 }

@@ -36,7 +36,7 @@ ERR_SCRATCH_LIMIT = 9
 
 F64, F32, BF16 = 0, 1, 2
 ACCUM = {"naive": 0, "comp": 1, "f64": 2}
-ABI_VERSION = 2  # LSEFIT_ABI_VERSION the structures below are laid out for
+ABI_VERSION = 3  # LSEFIT_ABI_VERSION the structures below are laid out for
 MAX_DEGREE = 8
 MAX_DEGREE_CHEBYSHEV = 16  # Chebyshev basis with FP64 accumulation
 

@@ -63,3 +63,31 @@ def test_torchrun_reference_arm_one_line():
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["cpu_baseline"]["host"]["nproc"] >= 1
+
+
+def test_gpus_flag_without_launcher_spawns_ranks():
+    """`bench.py --gpus 2` without torchrun starts two ranks itself (RANK,
+    WORLD_SIZE, a 127.0.0.1 rendezvous in each environment); the reference arm
+    prints one line from rank 0 and every rank exits 0."""
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_PORT")}
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1",
+           "--warmup", "0", "--n", "65536"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2
+
+
+def test_gpus_flag_more_than_the_node_has_fails_loudly():
+    """The GPU arm asked for more ranks than the node has GPUs exits non-zero
+    with a message instead of running fewer ranks."""
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_PORT")}
+    import torch
+    want = (torch.cuda.device_count() if torch.cuda.is_available() else 0) + 1
+    want = max(want, 2)
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", str(want), "--steps", "1", "--warmup", "3"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300, env=env)
+    assert r.returncode != 0
+    assert f"--gpus {want}" in r.stderr and not [l for l in r.stdout.splitlines() if l.startswith("{")]

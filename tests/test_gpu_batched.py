@@ -2,14 +2,16 @@
 
 Each series is compared with the oracle's fit of the same stored points on
 the same map (FP32-rounded constants for FP32 arithmetic, FP64 otherwise).
-Tolerances on the mapped-basis coefficients Xt (relative 2-norm): 1e-6 for
-FP64 accumulation; 1e-5 for compensated FP32 with m <= 3; otherwise
-max(1e-5, cond(A_t) * 2^-24 * 4m) (the per-point FP32 powers carry about
-k * 2^-24 relative error).  Statuses must match the oracle's exactly.
+Statuses must match the oracle's exactly.  Coefficients follow the policy of
+tests/gates.py: the mapped-basis Xt within max(1e-6 | 1e-5, cond(A_t) eps 4m)
+wherever that bound is at most 1e-3 (reported beyond, where the data leave
+the coefficients undetermined), and always within the backward-error gate of
+the accumulation.  Saved sums within the summation bound of the accumulation.
 """
 import numpy as np
 import pytest
 
+import gates
 import oracle
 import synth
 
@@ -29,18 +31,11 @@ def _hankel(S, m):
     return np.array([[S[j + k] for k in range(m + 1)] for j in range(m + 1)])
 
 
-def _tol(accum, m, S):
-    """1e-6 for FP64 accumulation and 1e-5 for compensated FP32 (degree <= 3 on
-    a well-conditioned mapped system); in general the bound grows with the
-    condition of the mapped Hankel matrix: cond(A_t) * eps * 4m, with eps the
-    unit roundoff of the per-point arithmetic (2^-53 FP64, 2^-24 FP32)."""
-    cond = np.linalg.cond(_hankel(S, m))
-    if accum == "f64":
-        return max(1e-6, cond * 2.0 ** -53 * 4 * m)
-    return max(1e-5, cond * EPS32 * 4 * m)
-
-
-def check_batch(L, b, res, accum, stored_x=None, stored_y=None, series=None, fp32_map=None):
+def check_batch(L, b, res, accum, stored_x=None, stored_y=None, series=None, fp32_map=None, sums_every=1,
+                stats=None):
+    """Check series `series` (all by default) against the oracle; the saved sums of
+    every sums_every-th checked series.  stats (a dict) collects the largest
+    forward and backward errors and the count of forward-reported series."""
     if fp32_map is None:
         fp32_map = accum != "f64"  # FP64 arithmetic maps with FP64 constants
     X = res["X"].cpu().numpy()
@@ -66,9 +61,15 @@ def check_batch(L, b, res, accum, stored_x=None, stored_y=None, series=None, fp3
             continue
         if b.get("interval") is not None:
             assert mp[s, 0] == r["c"] and mp[s, 1] == r["s"], s
-        tol = _tol(accum, m, r["S"])
-        e = np.linalg.norm(Xt[s, : m + 1] - r["Xt"]) / np.linalg.norm(r["Xt"])
-        assert e <= tol, (s, e, tol, m, hi - lo)
+        A = gates.hankel(r["S"], m)
+        try:
+            ef, tol, eta = gates.check_coefficients(Xt[s, : m + 1], r["Xt"], A, r["T"], accum, m)
+        except AssertionError as exc:
+            raise AssertionError((s, hi - lo) + tuple(exc.args)) from None
+        if stats is not None:
+            stats["forward_max"] = max(stats.get("forward_max", 0.0), ef if tol is not None else 0.0)
+            stats["backward_max"] = max(stats.get("backward_max", 0.0), eta)
+            stats["reported"] = stats.get("reported", 0) + (tol is None)
         assert np.all(X[s, m + 1:] == 0.0) and np.all(Xt[s, m + 1:] == 0.0)
         if b.get("interval") is not None:
             # the x-basis coefficients (the un-map of Xt) give the same polynomial: values
@@ -79,11 +80,21 @@ def check_batch(L, b, res, accum, stored_x=None, stored_y=None, series=None, fp3
             pw = np.arange(m + 1)
             f_ref = (r["Xt"][None, :] * tt[:, None] ** pw).sum(axis=1)
             terms = X[s, : m + 1][None, :] * xx[:, None] ** pw
-            slack = 2 * tol * np.linalg.norm(r["Xt"]) * (m + 1) + 1e-11 * np.abs(terms).sum(axis=1)
-            assert np.all(np.abs(terms.sum(axis=1) - f_ref) <= slack), (s, m)
-        # saved sums: S_0 exact, the rest close to the oracle's
+            if tol is not None:
+                slack = 2 * tol * np.linalg.norm(r["Xt"]) * (m + 1) + 1e-11 * np.abs(terms).sum(axis=1)
+                assert np.all(np.abs(terms.sum(axis=1) - f_ref) <= slack), (s, m)
+        # saved sums: S_0 exact, the others within the summation bound of the
+        # accumulation, scaled by sum |t|^k (|y|) of the same mapped points
         assert sums[s, 0] == hi - lo
-        np.testing.assert_allclose(sums[s, 1: 2 * m + 1], r["S"][1:], rtol=1e-4, atol=1e-4 * (hi - lo))
+        if checked % sums_every == 0:
+            t = xs[lo:hi] if b.get("interval") is None else r["s"] * (xs[lo:hi] - r["c"])
+            Sa, Ta = oracle.powersums(np.abs(t), np.abs(ys[lo:hi]), m)
+            lane = -(-(hi - lo) // 32)
+            for k in range(1, 2 * m + 1):
+                assert abs(sums[s, k] - r["S"][k]) <= gates.sums_bound_for(accum, k, Sa[k], lane), (s, k)
+            for k in range(m + 1):
+                assert abs(sums[s, 2 * m + 1 + k] - r["T"][k]) <= \
+                    gates.sums_bound_for(accum, k + 1, Ta[k], lane), (s, "T", k)
         checked += 1
     return checked
 
@@ -258,19 +269,20 @@ def test_cuda_graph_replay(L):
         assert torch.equal(torch.nan_to_num(out["X"]), torch.nan_to_num(ref))
 
 
-def test_full_size_ragged_sampled(L):
-    # the 65,536-series workload at the launch configuration the benchmark times;
-    # a sample of series is checked against the oracle one by one
+def test_full_size_ragged_all_series(L):
+    """The 65,536-series workload at the launch configuration the benchmark times
+    (the default plan: degree classes, warp tasks up to 65,536 points): every
+    series' status and coefficients against the oracle, the saved sums of one
+    series in 16."""
     b = synth.ragged_batch()
     _, _, res, plan = _run(L, b, "comp")
     st = res["status"].cpu().numpy()
     assert np.all(st == 0)
-    rng = np.random.default_rng(41)
-    sample = list(rng.choice(len(b["degree"]), 300, replace=False))
-    # include the longest and shortest series
-    lens = np.diff(b["offsets"])
-    sample += [int(np.argmax(lens)), int(np.argmin(lens))]
-    assert check_batch(L, b, res, "comp", series=sample) == len(sample)
+    stats = {}
+    S = len(b["degree"])
+    assert check_batch(L, b, res, "comp", sums_every=16, stats=stats) == S
+    print(f"ragged 65536: forward max {stats['forward_max']:.3g}, backward max {stats['backward_max']:.3g}, "
+          f"forward reported {stats['reported']}")
 
 
 # --- the Chebyshev basis in the batched kernel ----------------------------------------
@@ -291,10 +303,10 @@ def _check_cheb(L, b, res, accum, xs, ys, series=None):
         assert got == r["status"], (s, got, r["status"], hi - lo, m)
         if r["status"] != "ok":
             continue
-        cond = np.linalg.cond(r["G"])
-        tol = max(1e-6, cond * 2.0 ** -53 * 4 * m) if accum == "f64" else max(1e-5, cond * EPS32 * 4 * m)
-        e = np.linalg.norm(Xt[s, : m + 1] - r["Xb"]) / np.linalg.norm(r["Xb"])
-        assert e <= tol, (s, e, tol, m, hi - lo)
+        ef, tol, eta = gates.check_coefficients(Xt[s, : m + 1], r["Xb"], r["G"], r["b"], accum, m)
+        if tol is None:
+            checked += 1
+            continue
         xx = np.linspace(b["interval"][s][0], b["interval"][s][1], 5)
         f_ref = np.polynomial.chebyshev.chebval(r["s"] * (xx - r["c"]), r["Xb"])
         terms = X[s, : m + 1][None, :] * xx[:, None] ** np.arange(m + 1)

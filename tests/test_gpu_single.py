@@ -1,18 +1,20 @@
 """Parity of the single-series CUDA path (lsefit_powersums + lsefit_solve) with the oracle.
 
-Tolerances (relative 2-norm errors):
-  * FP64 accumulation: 1e-6 on the coefficients;
-  * compensated FP32, m <= 3, x mapped to [-1, 1]: 1e-5 on the mapped-basis
-    coefficients Xt;
-  * other FP32 cases: a bound derived from the arithmetic,
-    cond(A_t) * 2^-24 * 4m, on Xt (per-point powers carry about k * 2^-24
-    relative error; the summation itself is compensated).
+Tolerances (relative 2-norm errors of the mapped-basis coefficients Xt; the
+policy and its reasons are in tests/gates.py):
+  * FP64 accumulation: 1e-6;
+  * compensated FP32 on x mapped to [-1, 1]: 1e-5 at every degree up to 8
+    (measured at most 3.1e-7 at m = 8, cond(A) = 3e5);
+  * every ok result also passes the backward-error gate of its accumulation
+    (the GPU's Xt in the oracle's own normal equations), which does not
+    depend on cond(A).
 Where the oracle's own result is ill-determined (cond(A) * eps64 not small)
 only the mapped basis is compared.
 """
 import numpy as np
 import pytest
 
+import gates
 import oracle
 import synth
 
@@ -112,14 +114,11 @@ def test_fp32_mapped_unscaled_interval(L, m, accum):
     assert L.status_names(out["status"]) == ["ok"]
     mp = out["map"].cpu().numpy()
     assert mp[0] == ref["c"] and mp[1] == ref["s"]
-    cond = np.linalg.cond(_hankel(ref["S"], m))
-    if accum == "f64":
-        tol = 1e-6
-    elif m <= 3:
-        tol = 1e-5
-    else:
-        tol = cond * EPS32 * 4 * m
-    assert _rel(out["Xt"].cpu().numpy(), ref["Xt"]) <= tol, (cond, tol)
+    tol = 1e-6 if accum == "f64" else 1e-5
+    Xt = out["Xt"].cpu().numpy()
+    assert _rel(Xt, ref["Xt"]) <= tol, tol
+    A = _hankel(ref["S"], m)
+    assert gates.backward_error(A, ref["T"], Xt) <= gates.backward_gate(accum)
 
 
 @pytest.mark.parametrize("m", [1, 3, 5])
@@ -132,9 +131,10 @@ def test_bf16_storage(L, m):
     for accum in ("comp", "f64"):
         out = L.fit(_bf16_dev(xb), _bf16_dev(yb), m, accum=accum, interval=(-1.0, 1.0))
         assert L.status_names(out["status"]) == ["ok"]
-        cond = np.linalg.cond(_hankel(ref["S"], m))
-        tol = 1e-6 if accum == "f64" else max(1e-5, cond * EPS32 * 4 * m)
-        assert _rel(out["Xt"].cpu().numpy(), ref["Xt"]) <= tol
+        Xt = out["Xt"].cpu().numpy()
+        # BF16 storage, m <= 5: measured at most 3.9e-7 (compensated) on the 2^24 grid
+        assert _rel(Xt, ref["Xt"]) <= (1e-6 if accum == "f64" else 1e-5)
+        assert gates.backward_error(_hankel(ref["S"], m), ref["T"], Xt) <= gates.backward_gate(accum)
 
 
 # --- ragged sizes, alignment and tails ---------------------------------------------
@@ -249,9 +249,8 @@ def test_fused_fit_degrees(L, m, m_lo):
     Xt = out["Xt"].cpu().numpy()
     for r, deg in enumerate(range(m_lo, m + 1)):
         ref = oracle.fit_interval(d["x"], d["y"], deg, -1.0, 1.0, fp32=True)
-        cond = np.linalg.cond(_hankel(ref["S"], deg))
-        tol = 1e-5 if deg <= 3 else cond * EPS32 * 4 * deg
-        assert _rel(Xt[r, : deg + 1], ref["Xt"]) <= tol, (deg, cond)
+        assert _rel(Xt[r, : deg + 1], ref["Xt"]) <= 1e-5, deg
+        assert gates.backward_error(_hankel(ref["S"], deg), ref["T"], Xt[r, : deg + 1]) <= gates.BACKWARD["comp"]
         assert np.all(X[r, deg + 1:] == 0.0)
         # same as the two-launch path
         X2, Xt2, st2 = L.solve(out["sums"], deg, m, out["map"])
@@ -301,3 +300,45 @@ def test_fp64_mapped_coefficients(L, m):
     assert L.status_names(out["status"]) == ["ok"]
     assert _rel(out["Xt"].cpu().numpy(), ref["Xt"]) <= 1e-9
     assert _rel(out["X"].cpu().numpy(), ref["X"]) <= 1e-9
+
+
+# --- the benchmark's own call at its full size ----------------------------------------------
+
+def test_full_size_bench_call(L):
+    """The call bench.py times, on its workload: fit_degrees(x, y, 3, 1, "comp") on the
+    2^28-point FP32 series (x on [-1, 1], no interval), in the launch configuration of
+    that size (304 blocks, ~860 grid-stride rounds per thread).  Every degree's X and Xt
+    against the oracle's fit of the same stored points, the saved sums within the
+    compensated-FP32 summation bound, and a second call bit-identical to the first."""
+    n = 1 << 28
+    d = synth.single_large(n=n, m=3, seed=synth.SEED_SINGLE_LARGE)
+    x, y = _dev(d["x"]), _dev(d["y"])
+    out = L.fit_degrees(x, y, 3, 1, "comp")
+    torch.cuda.synchronize()
+    assert L.status_names(out["status"]) == ["ok"] * 3
+    X = out["X"].cpu().numpy()
+    Xt = out["Xt"].cpu().numpy()
+    sums = out["sums"].cpu().numpy()
+    again = L.fit_degrees(x, y, 3, 1, "comp")
+    assert torch.equal(again["X"], out["X"]) and torch.equal(again["sums"], out["sums"])
+    del x, y, again
+    x64 = d["x"].astype(np.float64)
+    y64 = d["y"].astype(np.float64)
+    ref = oracle.fit(x64, y64, 3, eps=oracle.EPS32)
+    assert ref["status"] == "ok"
+    S, T = ref["S"], ref["T"]
+    for r, deg in enumerate((1, 2, 3)):
+        st, Xo = oracle.solve(S[: 2 * deg + 1], T[: deg + 1], deg, eps=oracle.EPS32)
+        assert st == "ok"
+        assert _rel(Xt[r, : deg + 1], Xo) <= 1e-5, deg
+        assert _rel(X[r, : deg + 1], Xo) <= 1e-5, deg  # no interval: X = Xt
+        assert np.all(X[r, deg + 1:] == 0.0)
+        assert gates.backward_error(_hankel(S, deg), T[: deg + 1], Xt[r, : deg + 1]) <= gates.BACKWARD["comp"]
+    # sums: S_0 exact; the others within the bound of the compensated FP32 pass
+    # (batches of 8 points per packed lane at degree 3), scaled by sum |x|^k (|y|)
+    Sa, Ta = oracle.powersums(np.abs(x64), np.abs(y64), 3)
+    assert sums[0] == n
+    for k in range(1, 7):
+        assert abs(sums[k] - S[k]) <= gates.sums_bound(k, Sa[k], batch=8), k
+    for k in range(4):
+        assert abs(sums[7 + k] - T[k]) <= gates.sums_bound(k + 1, Ta[k], batch=8), k

@@ -580,3 +580,72 @@ def test_residuals_general_table1_and_orthogonality():
     scale = np.sum(np.abs(y)) * 1e3
     assert np.max(np.abs(vtr_c)) <= 1e-12 * scale
     assert np.max(np.abs(vtr_m[:1])) <= 1e-9 * scale
+
+
+# --- the all-core timing variant of the power sums -----------------------------------------
+
+@pytest.mark.parametrize("threads", [1, 2, 3, 8, 16])
+@pytest.mark.parametrize("m", [1, 3, 8])
+def test_powersums_threads_bit_exact_int(threads, m):
+    """Small integers: every partial sum is an exact FP64 integer, so any order of
+    addition gives the exact power sums: the all-core variant equals int64 sums."""
+    rng = np.random.default_rng(900 + threads + m)
+    n = 10_007
+    xi = rng.integers(-6, 7, n)
+    yi = rng.integers(-50, 51, n)
+    S, T = oracle.powersums_threads(xi.astype(np.float64), yi.astype(np.float64), m, threads=threads)
+    x64 = xi.astype(np.int64)
+    assert S[0] == n
+    for k in range(1, 2 * m + 1):
+        assert S[k] == float(int(np.sum(x64 ** k))), k
+    for k in range(m + 1):
+        assert T[k] == float(int(np.sum(x64 ** k * yi))), k
+
+
+@pytest.mark.parametrize("threads", [2, 5, 16])
+def test_powersums_threads_within_the_summation_bound(threads):
+    """Random data: the all-core sums and the sequential oracle's add the same
+    terms in different orders, so they differ by at most twice the bound of one
+    recursive sum, 2 (n - 1) 2^-53 sum |t|^k (|y|), and are repeatable."""
+    d = synth.single_large(n=200_003, m=3, seed=901)
+    x, y = d["x"].astype(np.float64), d["y"].astype(np.float64)
+    cs = (0.25, 1.5)
+    for m in (1, 4):
+        S1, T1 = oracle.powersums(x, y, m, cs)
+        St, Tt = oracle.powersums_threads(x, y, m, cs, threads=threads)
+        t = cs[1] * (x - cs[0])
+        Sa, Ta = oracle.powersums(np.abs(t), np.abs(y), m)
+        bound = 2 * (x.size - 1) * 2.0 ** -53
+        assert St[0] == S1[0] == x.size
+        assert np.all(np.abs(St[1:] - S1[1:]) <= bound * Sa[1:])
+        assert np.all(np.abs(Tt - T1) <= bound * Ta)
+        S2, T2 = oracle.powersums_threads(x, y, m, cs, threads=threads)
+        assert np.array_equal(St, S2) and np.array_equal(Tt, T2)
+    # one thread is the sequential routine itself
+    S1, T1 = oracle.powersums(x, y, 2)
+    S2, T2 = oracle.powersums_threads(x, y, 2, threads=1)
+    assert np.array_equal(S1, S2) and np.array_equal(T1, T2)
+
+
+def test_powersums_threads_edges():
+    # fewer points than threads (empty ranges), no points, bad thread counts
+    S, T = oracle.powersums_threads(np.array([1.0, 2.0, 3.0]), np.array([1.0, 1.0, 1.0]), 2, threads=8)
+    assert list(S) == [3.0, 6.0, 14.0, 36.0, 98.0] and list(T) == [3.0, 6.0, 14.0]
+    S, T = oracle.powersums_threads(np.zeros(0), np.zeros(0), 1, threads=4)
+    assert list(S) == [0.0, 0.0, 0.0] and list(T) == [0.0, 0.0]
+    for bad in (0, -1, 5000):
+        with pytest.raises(ValueError):
+            oracle.powersums_threads(np.ones(4), np.ones(4), 1, threads=bad)
+
+
+def test_fit_threads_matches_fit():
+    d = synth.single_fp64(n=50_000)
+    a = oracle.fit(d["x"], d["y"], 3)
+    b = oracle.fit_threads(d["x"], d["y"], 3, threads=6)
+    assert a["status"] == b["status"] == "ok"
+    assert np.linalg.norm(a["X"] - b["X"]) <= 1e-9 * np.linalg.norm(a["X"])
+    st, c, s = oracle.map_constants(0.0, 10.0, False)
+    a = oracle.fit(d["x"], d["y"], 2, (c, s))
+    b = oracle.fit_threads(d["x"], d["y"], 2, (c, s), threads=3)
+    assert np.linalg.norm(a["X"] - b["X"]) <= 1e-12 * np.linalg.norm(a["X"])
+    assert np.linalg.norm(a["Xt"] - b["Xt"]) <= 1e-12 * np.linalg.norm(a["Xt"])
