@@ -667,7 +667,7 @@ def run_ragged_batch(args, dist: Dist):
     if args.tuning:
         tuning, tried = json.loads(args.tuning), []
     else:
-        tuning, tried = autotune.tune_batched(x, y, off, deg, iv, m_max=m_max, accum=args.accum)
+        tuning, tried = autotune.tune_batched(x, y, off, deg, iv, m_max=m_max, accum=args.accum, basis=args.basis)
     t_tune = time.perf_counter() - t_tune
     t_plan = time.perf_counter()
     plan = L.BatchPlan(b["offsets"], m_max, tuning=tuning, device=dev, degree=b["degree"])

@@ -404,6 +404,61 @@ int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* plan, doubl
                        double* Xt, double* sums, double* map, int32_t* status,
                        void* workspace, size_t workspace_bytes, lsefit_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Autotuning of the batched schedule
+ * ------------------------------------------------------------------------ */
+
+/* Largest candidate list lsefit_plan_autotune accepts. */
+#define LSEFIT_AUTOTUNE_MAX_CANDIDATES 32
+
+/* Copies the built-in candidate tunings into out[0 .. min(cap, count) - 1]
+ * (out may be NULL) and returns their count: every series a warp task under
+ * each of the three schedules, and the degree-class schedule with block tasks
+ * above 4,096 or 65,536 points in chunks of 65,536 or 262,144.  Host only. */
+int lsefit_autotune_candidates(lsefit_tuning* out, int cap);
+
+/* Device buffer sizes lsefit_plan_autotune needs for one layout: *task_ints
+ * = int32 elements of the largest task arrays over the candidates (block
+ * tasks then warp tasks), *workspace_bytes = the largest batched workspace.
+ * candidates NULL = the built-in list (n_candidates ignored).  Host only;
+ * num_sms as for lsefit_plan_build. */
+int lsefit_plan_autotune_sizes(const int64_t* offsets_host, const int32_t* degree_host, int64_t num_series,
+                               int m_max, const lsefit_tuning* candidates, int n_candidates, int num_sms,
+                               int64_t* task_ints, size_t* workspace_bytes);
+
+/*
+ * lsefit_plan_autotune -- measure candidate schedules of lsefit_fit_batched
+ * on the caller's batch and return the fastest (the batched fit computes the
+ * same Section II fit under every schedule; only the assignment of series to
+ * warps and blocks changes).  For each candidate: the plan is built on the
+ * host for the layout (offsets_host, degree_host), its task arrays copied
+ * into tasks_device, one warm-up fit, then `reps` fits timed with CUDA events
+ * on `stream`.  Synchronous: returns after the last measurement.  Outputs of
+ * the trial fits land in X and status (their content is the last
+ * candidate's fit).  Build the final plan with lsefit_plan_build(*best).
+ *  batch          host descriptor of the device batch (as lsefit_fit_batched).
+ *  offsets_host, degree_host   host copies of the layout (degree may be NULL).
+ *  candidates     host array of n_candidates tunings, or NULL for the
+ *                 built-in list (lsefit_autotune_candidates).
+ *  reps           timed fits per candidate, >= 1.
+ *  tasks_device   device int32[task_ints], 16-byte aligned (from
+ *                 lsefit_plan_autotune_sizes); overwritten per candidate.
+ *  workspace      device, >= the size lsefit_plan_autotune_sizes gives,
+ *                 256-byte aligned.
+ *  X, status      device outputs as for lsefit_fit_batched.
+ *  best           host, written: the resolved tuning of the fastest candidate.
+ *  ms_per_candidate  host float[n_candidates] or NULL: mean ms per fit.
+ * Allocates no device memory (two CUDA events are created and destroyed).
+ */
+int lsefit_plan_autotune(const lsefit_batch* batch, const int64_t* offsets_host, const int32_t* degree_host,
+                         const lsefit_tuning* candidates, int n_candidates, int reps, int32_t* tasks_device,
+                         int64_t task_ints, void* workspace, size_t workspace_bytes, double* X,
+                         int32_t* status, lsefit_stream_t stream, lsefit_tuning* best, float* ms_per_candidate);
+
+/* CUDA driver version (cudaDriverGetVersion) the library sees, 0 if none;
+ * part of the key under which measured tunings are cached. */
+int lsefit_driver_version(void);
+
 /* Bytes of workspace lsefit_range needs for `plan`. */
 size_t lsefit_range_workspace_size(const lsefit_plan* plan);
 

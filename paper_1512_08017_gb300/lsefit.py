@@ -103,6 +103,10 @@ SIGNATURES = {
     "lsefit_residuals": (_INT, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "lsefit_range_workspace_size": (_SZ, [_VP]),
     "lsefit_range": (_INT, [_VP, _VP, _VP, _VP, _SZ, _VP]),
+    "lsefit_autotune_candidates": (_INT, [_VP, _INT]),
+    "lsefit_plan_autotune_sizes": (_INT, [_VP, _VP, _I64, _INT, _VP, _INT, _INT, _VP, _VP]),
+    "lsefit_plan_autotune": (_INT, [_VP, _VP, _VP, _VP, _INT, _INT, _VP, _I64, _VP, _SZ, _VP, _VP, _VP, _VP, _VP]),
+    "lsefit_driver_version": (_INT, []),
     "lsefit_backward_workspace_size": (_SZ, [_VP]),
     "lsefit_backward": (_INT, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
 }

@@ -63,7 +63,7 @@ def check_batch(L, b, res, accum, stored_x=None, stored_y=None, series=None, fp3
             assert mp[s, 0] == r["c"] and mp[s, 1] == r["s"], s
         A = gates.hankel(r["S"], m)
         try:
-            ef, tol, eta = gates.check_coefficients(Xt[s, : m + 1], r["Xt"], A, r["T"], accum, m)
+            ef, tol, eta = gates.check_coefficients(Xt[s, : m + 1], r["Xt"], A, r["T"], accum, m, n=hi - lo)
         except AssertionError as exc:
             raise AssertionError((s, hi - lo) + tuple(exc.args)) from None
         if stats is not None:
@@ -303,7 +303,7 @@ def _check_cheb(L, b, res, accum, xs, ys, series=None):
         assert got == r["status"], (s, got, r["status"], hi - lo, m)
         if r["status"] != "ok":
             continue
-        ef, tol, eta = gates.check_coefficients(Xt[s, : m + 1], r["Xb"], r["G"], r["b"], accum, m)
+        ef, tol, eta = gates.check_coefficients(Xt[s, : m + 1], r["Xb"], r["G"], r["b"], accum, m, n=hi - lo)
         if tol is None:
             checked += 1
             continue

@@ -49,14 +49,14 @@ def _stored(t):
     return t.double().cpu().numpy()
 
 
-def _check(L, out, ref, accum, m, row=0):
+def _check(L, out, ref, accum, m, row=0, n=1 << 24):
     st = L.status_names(out["status"])[row]
     assert st == ref["status"], (st, ref["status"])
     if st != "ok":
         assert np.all(np.isnan(out["X"][row, : m + 1].cpu().numpy()))
         return None
     e, _, _ = gates.check_coefficients(out["Xb"][row, : m + 1].cpu().numpy(), ref["Xb"], ref["G"], ref["b"],
-                                       accum, m, _base(accum))
+                                       accum, m, _base(accum), n=n)
     return e
 
 

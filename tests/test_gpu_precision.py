@@ -88,7 +88,7 @@ def test_precision_grid(L):
                         row["xt_norm"], row["xt_max"] = _errs(out["Xt"].cpu().numpy(), ref["Xt"])
                         row["x_norm"], row["x_max"] = _errs(out["X"].cpu().numpy(), ref["X"])
                         row["eta"] = gates.backward_error(_hankel(ref["S"], m), ref["T"], out["Xt"].cpu().numpy())
-                        if row["eta"] > gates.backward_gate(accum):
+                        if row["eta"] > gates.backward_gate(accum, N):
                             failures.append(("backward", row))
                     rows.append(row)
                     eps = 2.0 ** -53 if accum == "f64" else EPS32
@@ -121,7 +121,7 @@ def test_precision_grid(L):
                 e1 = f"{r['xt_norm']:.2e} / {r['xt_max']:.2e}" if "xt_norm" in r else "—"
                 e2 = f"{r['x_norm']:.2e} / {r['x_max']:.2e}" if "x_norm" in r else "—"
                 gate = f"{r['tol']:.1e}" if r.get("tol") else "reported"
-                eta = f"{r['eta']:.1e} ({gates.backward_gate(r['accum']):.0e})" if "eta" in r else "—"
+                eta = f"{r['eta']:.1e} ({gates.backward_gate(r['accum'], N):.1e})" if "eta" in r else "—"
                 f.write(f"| {r['m']} | {r['storage']} | {r['map']} | {r['accum']} | {r['status']} / {r['oracle']} "
                         f"| {r['cond']:.2e} | {e1} | {e2} | {gate} | {eta} |\n")
     assert not failures, failures[:5]

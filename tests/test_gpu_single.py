@@ -118,7 +118,7 @@ def test_fp32_mapped_unscaled_interval(L, m, accum):
     Xt = out["Xt"].cpu().numpy()
     assert _rel(Xt, ref["Xt"]) <= tol, tol
     A = _hankel(ref["S"], m)
-    assert gates.backward_error(A, ref["T"], Xt) <= gates.backward_gate(accum)
+    assert gates.backward_error(A, ref["T"], Xt) <= gates.backward_gate(accum, d["x"].size)
 
 
 @pytest.mark.parametrize("m", [1, 3, 5])
@@ -134,7 +134,7 @@ def test_bf16_storage(L, m):
         Xt = out["Xt"].cpu().numpy()
         # BF16 storage, m <= 5: measured at most 3.9e-7 (compensated) on the 2^24 grid
         assert _rel(Xt, ref["Xt"]) <= (1e-6 if accum == "f64" else 1e-5)
-        assert gates.backward_error(_hankel(ref["S"], m), ref["T"], Xt) <= gates.backward_gate(accum)
+        assert gates.backward_error(_hankel(ref["S"], m), ref["T"], Xt) <= gates.backward_gate(accum, xb.size)
 
 
 # --- ragged sizes, alignment and tails ---------------------------------------------
