@@ -858,10 +858,11 @@ def run_diff_batch(args, dist: Dist):
     def fwd():
         L.fit_batched(x, y, off, deg, iv, m_max=m, accum=args.accum, plan=plan, out=fwd_out)
 
+    w2 = 2.0 * w  # dL/dX of the user's loss L = sum w X^2 is 2 w X: one multiply per step
+
     def fwd_bwd():
         fwd()
-        torch.mul(fwd_out["X"], w, out=gX)
-        gX.mul_(2.0)  # dL/dX of L = sum w X^2 (the user's loss)
+        torch.mul(fwd_out["X"], w2, out=gX)
         L.backward(x, y, off, deg, fwd_out, gX, dx=dx, dy=dy, status=bst, accum=args.accum)
 
     gf = _graph(fwd, stream)
@@ -944,8 +945,7 @@ def run_diff_batch(args, dist: Dist):
                                  ctypes.c_void_p(sums.data_ptr() + 8 * (3 * m + 2) * s_),
                                  ctypes.c_void_p(mp.data_ptr() + 16 * s_), ctypes.c_void_p(st.data_ptr() + 4 * s_),
                                  ctypes.c_void_p(ws.data_ptr()), wsz, sh)
-            torch.mul(Xs, w, out=gX)
-            gX.mul_(2.0)
+            torch.mul(Xs, w2, out=gX)
             for s_ in range(S):
                 B.lib.lsefit_backward(ctypes.byref(batches[s_]), ctypes.byref(plan1.plan),
                                       ctypes.c_void_p(sums.data_ptr() + 8 * (3 * m + 2) * s_),
@@ -1004,7 +1004,7 @@ def run_diff_batch(args, dist: Dist):
         "plain_per_series": plain,
         "speedup_vs_plain": (plain["ms_per_step"] / msb) if plain else None,
         "coef_err": coef,
-        "cpu_baseline": None, "e2e": e2e, "clocks": clk, "gpu_launches": 6 * args.steps,
+        "cpu_baseline": None, "e2e": e2e, "clocks": clk, "gpu_launches": 4 * args.steps,
     }
 
 

@@ -314,7 +314,9 @@ typedef struct lsefit_tuning {
     int32_t schedule;         /* how warps take warp tasks:
                                  1 = from one queue, in plan order;
                                  2 = fixed snake order (round r gives warp w task r*W + w,
-                                     or r*W + W-1-w on odd rounds; W warps in the grid);
+                                     or r*W + W-1-w on odd rounds; W warps in the grid,
+                                     numbered warp-major: w = warp * blocks + block, so a
+                                     partly filled round is shared evenly by the SMs);
                                  3 (0 = default) = one queue per degree class, longest
                                      first; every block starts on a class (blocks shared
                                      out in proportion to the classes' points times a

@@ -12,7 +12,10 @@
 // Launch 1 solves for lambda, one series per thread (FP64, padded
 // elimination).  Launch 2 streams the points once more with the forward
 // plan's tasks, recomputing t and the polynomial values by Horner's rule
-// with derivative (packed FP32 pairs; FP64 for FP64 data).
+// with derivative (packed FP32 pairs; FP64 for FP64 data).  Launch 2 may start
+// while launch 1 runs (programmatic dependent launch) and waits for it on the
+// GPU before it reads lambda; it takes the warp tasks in reverse plan order,
+// so the points the forward pass read last, still in L2, come first.
 #include <cstring>
 
 #include "lsefit_device.cuh"
@@ -54,6 +57,7 @@ template <int NMAX>
 __global__ void lambda_kernel(int64_t S, int m_max, double eps, const int32_t* degree, const double* sums,
                               const double* map, const double* gX, const double* Xt, double* lambda,
                               float* lamf, float* xtf, float2* mapf, int32_t* status, unsigned* counters) {
+    griddep_launch_dependents();  // the point pass may start its set-up now
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < 3) counters[s] = 0u;  // the point pass's queue counters (no initialization needed)
     if (s >= S) return;
@@ -81,7 +85,19 @@ __global__ void lambda_kernel(int64_t S, int m_max, double eps, const int32_t* d
     int st = fit_precheck<NMAX>(m, Srow, Srow + 2 * m + 1, ok);
     constexpr int N = NMAX + 1;
     double gt[N], z[N];
-    if (st == LSEFIT_OK) {
+    // identity map (c = 0, s = 1): gt = gX, no transform (skipped when every
+    // active lane of the warp has it: FP64 instructions cost the warp the same
+    // for one lane as for 32)
+    const bool ident = c == 0.0 && sc == 1.0;
+    if (__all_sync(__activemask(), ident) && st == LSEFIT_OK) {
+        const double* g = gX + s * nc;
+#pragma unroll
+        for (int k = 0; k < N; ++k) gt[k] = k <= m ? g[k] : 0.0;
+        bool fin = true;
+#pragma unroll
+        for (int k = 0; k < N; ++k) fin = fin && finite_bits(gt[k]);
+        st = fin ? hankel_ge<NMAX>(m, Srow, gt, z, eps) : LSEFIT_ERR_NONFINITE;
+    } else if (st == LSEFIT_OK) {
         // gt_k = sum_{j<=k} C(k,j) s^k (-c)^(k-j) gX_j
         const double* g = gX + s * nc;
         double binom[N];
@@ -321,6 +337,8 @@ template <int DT>
 __global__ void __launch_bounds__(kBwBlock) grad_kernel(BwParams p) {
     __shared__ int s_task;
     const int tid = threadIdx.x, lane = tid & 31;
+    // lambda, the FP32 copies and the queue counters come from the lambda launch
+    griddep_wait();
     for (;;) {
         if (tid == 0) s_task = (int)atomicAdd(&p.counters[0], 1u);
         __syncthreads();
@@ -335,12 +353,14 @@ __global__ void __launch_bounds__(kBwBlock) grad_kernel(BwParams p) {
         const int64_t e = min(b + per, e0);
         grad_dispatch<DT>(p, s, b, e, tid, kBwBlock);
     }
+    // warp tasks in reverse plan order: the forward pass read the last tasks of
+    // the plan last, so their points are the ones still held in L2
     for (;;) {
         int t = 0;
         if (lane == 0) t = (int)atomicAdd(&p.counters[1], 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= p.n_warp_tasks) break;
-        const int64_t s = p.warp_tasks[t].x;
+        const int64_t s = p.warp_tasks[p.n_warp_tasks - 1 - t].x;
         grad_dispatch<DT>(p, s, p.offsets[s], p.offsets[s + 1], lane, 32);
     }
     __syncthreads();
@@ -399,7 +419,9 @@ extern "C" int lsefit_backward(const lsefit_batch* batch, const lsefit_plan* pla
     float* lamf = reinterpret_cast<float*>(ws + bw_off_lamf(plan));
     float* xtf = reinterpret_cast<float*>(ws + bw_off_xtf(plan));
     float2* mapf = reinterpret_cast<float2*>(ws + bw_off_mapf(plan));
-    const int threads = 64;
+    // one warp per block, so the solves (FP64-bound: an FP64 instruction costs a
+    // warp the same for one lane as for 32) spread over as many SMs as possible
+    const int threads = 32;
     const int64_t blocks = (b.num_series + threads - 1) / threads;
     auto lk = b.m_max <= 3 ? lambda_kernel<3> : b.m_max <= 5 ? lambda_kernel<5> : lambda_kernel<8>;
     lk<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(b.num_series, b.m_max, singular_eps(b.accum),
@@ -438,6 +460,10 @@ extern "C" int lsefit_backward(const lsefit_batch* batch, const lsefit_plan* pla
     const int64_t useful = (int64_t)plan->n_block_tasks + (plan->n_warp_tasks + 7) / 8;
     if (useful < grid) grid = useful;
     if (grid < 1) grid = 1;
-    gk<<<(unsigned)grid, kBwBlock, 0, (cudaStream_t)stream>>>(p);
-    return cudaGetLastError() == cudaSuccess ? LSEFIT_OK : LSEFIT_ERR_CUDA;
+    // the point pass starts while the lambda solves run and waits for them on the GPU
+    if (launch_after_prior(gk, dim3((unsigned)grid), dim3(kBwBlock), 0, (cudaStream_t)stream, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return LSEFIT_ERR_CUDA;
+    }
+    return LSEFIT_OK;
 }

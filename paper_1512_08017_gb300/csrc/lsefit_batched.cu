@@ -277,6 +277,11 @@ extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* 
         prep<<<(unsigned)pb, pt, 0, (cudaStream_t)stream>>>(p);
         if (cudaGetLastError() != cudaSuccess) return LSEFIT_ERR_CUDA;
     }
-    k<<<(unsigned)grid, kBBlock, smem, (cudaStream_t)stream>>>(p);
-    return cudaGetLastError() == cudaSuccess ? LSEFIT_OK : LSEFIT_ERR_CUDA;
+    // the persistent kernel starts while the preparation runs: it loads its first
+    // task records, then waits for the preparation's map constants and counters
+    if (launch_after_prior(k, dim3((unsigned)grid), dim3(kBBlock), smem, (cudaStream_t)stream, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return LSEFIT_ERR_CUDA;
+    }
+    return LSEFIT_OK;
 }

@@ -80,6 +80,7 @@ struct BParams {
 // ---------------------------------------------------------------------------
 template <bool FP32MAP>
 __global__ void batched_prep_kernel(BParams p) {
+    griddep_launch_dependents();  // the persistent kernel may start its set-up now
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < kCounters) p.counters[s] = 0u;
     if (s < p.n_block_tasks) p.tickets[s] = 0u;
@@ -216,15 +217,17 @@ struct Ring {
 
 // Producer cursor of a warp.  Warp tasks are drawn from one queue in plan
 // order (schedule 1), in a fixed snake order (schedule 2: round r gives warp
-// w task r*W + w, or r*W + W-1-w on odd rounds, W warps in the grid), or
+// w task r*W + w, or r*W + W-1-w on odd rounds, W warps in the grid numbered
+// warp-major, w = warp * blocks + block, so that a round that is only partly
+// filled still gives every SM the same share), or
 // from one queue per degree class (schedule 3): a block starts on the class
 // its index falls in when the blocks are shared out in proportion to the
 // classes' cost, points x cost per point of the degree (cls_block, set at
 // launch), and a warp whose class has run dry moves on to the next class with
 // tasks left, so the warps of an SM keep running the code of one degree.  In schedules 1 and 3 the first
 // kStaticRounds draws of a warp are fixed snake rounds over the warps of its
-// first queue and only later draws take an atomic ticket (offset past the
-// static rounds): a grid that starts with every warp hitting one counter
+// first queue (numbered warp-major too) and only later draws take an atomic
+// ticket (offset past the static rounds): a grid that starts with every warp hitting one counter
 // spends microseconds in its queue.  Three tasks are in the pipeline ahead
 // of the one being issued, one step per advance, so no advance waits on a
 // load: tq (lane 0) holds the next index, a (lane 0) the task record loaded
@@ -257,7 +260,9 @@ static __device__ __noinline__ int3 cursor_draw(int round, int cls, const BParam
     const int warp = threadIdx.x >> 5;
     if (p.sched == 2) {
         const long long nw = (long long)gridDim.x * kBWarps;
-        const long long wid = (long long)blockIdx.x * kBWarps + warp;
+        // warp-major numbering: consecutive indices go to the same warp slot of
+        // consecutive blocks, so a partly filled round is spread over every SM
+        const long long wid = (long long)warp * gridDim.x + blockIdx.x;
         const long long t = (long long)round * nw + ((round & 1) ? (nw - 1 - wid) : wid);
         round++;
         return make_int3(t < p.n_warp_tasks ? (int)t : kNone, round, cls);
@@ -272,7 +277,8 @@ static __device__ __noinline__ int3 cursor_draw(int round, int cls, const BParam
         const int nwc = (classes ? p.cls_block[c + 1] - blk0 : (int)gridDim.x) * kBWarps;
         const int nstatic = min(n, kStaticRounds * nwc);
         if (round < kStaticRounds) {  // the warp's first queue: fixed snake rounds
-            const int r = ((int)blockIdx.x - blk0) * kBWarps + warp;
+            const int nblk = nwc / kBWarps;
+            const int r = warp * nblk + ((int)blockIdx.x - blk0);  // warp-major, as in schedule 2
             const int local = round * nwc + ((round & 1) ? (nwc - 1 - r) : r);
             round++;
             if (local < nstatic) return make_int3(b + local, round, cls);
@@ -373,6 +379,10 @@ __device__ __forceinline__ void cursor_init(Cursor& cu, const BParams& p) {
     cu.tq = 0x7fffffff;
     cu.round = 0;
     cu.cls = 0;
+    // map constants and queue counters come from the preparation launch (a
+    // first draw can already reach an atomic queue when its static round is
+    // empty)
+    griddep_wait();
     if ((threadIdx.x & 31) == 0) {
         const int3 d = cursor_draw(0, first_class(p), p);
         cu.tq = d.x;
@@ -503,6 +513,7 @@ __device__ __noinline__ void pend_solve_entry(const BParams& p, unsigned char* p
     double* x = p.X + s * nc;
     const double* T = sm + 2 * m + 1;
     int st;
+    if (CHEB && active) cheb_moments_from_products(m, sm);  // degrees m+1..2m were kept as product sums
     if (CHEB) {
         // Chebyshev basis: G from the moments (sm[0] = n), Xt holds the Chebyshev coefficients
         switch (mw) {
@@ -905,7 +916,8 @@ __global__ void __launch_bounds__(kBBlock, 1) batched_kernel(BParams p) {
     Pend<NMAX> q;
     q.bind(pend_block + warp * PendLayout<NMAX>::kWarpBytes);
 
-    // phase 1: block tasks
+    // phase 1: block tasks (their queue counter is cleared by the preparation launch)
+    if (p.n_block_tasks > 0) griddep_wait();
     for (; p.n_block_tasks > 0;) {
         if (tid == 0) s_task = (int)atomicAdd(&p.counters[0], 1u);
         __syncthreads();

@@ -174,6 +174,17 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization may start while the kernel before it on the stream is still
+// running: griddep_wait() returns once that kernel has completed and its
+// writes are visible (at once when the launch carries no such dependency),
+// and griddep_launch_dependents() lets the kernel after this one start early.
+// Both are hardware-managed: no thread spins on memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::); }
+
+// ---------------------------------------------------------------------------
 // Map constants.  c = (lo + hi) / 2, s = 2 / (hi - lo) in FP64, rounded once
 // to FP32 when the points are mapped in FP32.  Identity without an interval.
 // Returns false for an interval that is not finite or has hi <= lo.
@@ -261,36 +272,55 @@ struct AccF32 {
     // T_0 = 1 would otherwise make an empty lane with t = 0 count in T_2).
     template <bool FIRST>
     __device__ __forceinline__ void add_pair(u64 t, u64 y, u64 seed = 0ull) {
-        u64 p = t;
-        u64 pm1 = seed;       // T_{k-2} (Chebyshev)
-        const u64 t2 = CHEB ? add2(t, t) : 0ull;
-        const u64 nt2 = CHEB ? mul2(t, pk2(-2.0f, -2.0f)) : 0ull;
-        if (FIRST) {
-            acc[2 * M] = y;
-            acc[0] = p;
-            acc[2 * M + 1] = mul2(p, y);
-        } else {
-            acc[2 * M] = add2(acc[2 * M], y);
-            acc[0] = add2(acc[0], p);
-            acc[2 * M + 1] = fma2(p, y, acc[2 * M + 1]);
+        if (!CHEB) {
+            add_pair_powers<FIRST>(t, y);
+            return;
+        }
+        // Chebyshev: v_k = sigma_k T_k by the recurrence up to k = M feeds the
+        // moments of degree 1..M and the right-hand sides; the slot of degree
+        // k = M+1..2M takes the product v_a v_b (a = k/2, b = k - a), whose sum
+        // is sigma_a sigma_b (C_k + C_{b-a}) / 2 by T_a T_b = (T_{a+b} + T_{b-a}) / 2.
+        // result() removes the sign; cheb_moments_from_products() then gives C_k.
+        u64 v[M + 1];
+        v[0] = seed;
+        v[1] = t;
+        const u64 t2 = add2(t, t);
+        const u64 nt2 = mul2(t, pk2(-2.0f, -2.0f));
+#pragma unroll
+        for (int k = 2; k <= M; ++k) v[k] = fma2((k & 1) ? t2 : nt2, v[k - 1], v[k - 2]);
+        acc[2 * M] = FIRST ? y : add2(acc[2 * M], y);
+#pragma unroll
+        for (int k = 1; k <= M; ++k) {
+            acc[k - 1] = FIRST ? v[k] : add2(acc[k - 1], v[k]);
+            acc[2 * M + k] = FIRST ? mul2(v[k], y) : fma2(v[k], y, acc[2 * M + k]);
         }
 #pragma unroll
-        for (int k = 2; k <= 2 * M; ++k) {
-            if (CHEB) {
-                // sigma_k sigma_{k-1} = -1 for even k, +1 for odd k
-                const u64 pk = fma2((k & 1) ? t2 : nt2, p, pm1);
-                pm1 = p;
-                p = pk;
-            } else {
-                p = mul2(p, t);
-            }
-            if (FIRST) {
-                acc[k - 1] = p;
-                if (k <= M) acc[2 * M + k] = mul2(p, y);
-            } else {
-                acc[k - 1] = add2(acc[k - 1], p);
-                if (k <= M) acc[2 * M + k] = fma2(p, y, acc[2 * M + k]);
-            }
+        for (int k = M + 1; k <= 2 * M; ++k) {
+            const int a = k / 2, b = k - k / 2;
+            acc[k - 1] = FIRST ? mul2(v[a], v[b]) : fma2(v[a], v[b], acc[k - 1]);
+        }
+    }
+
+    // Monomial basis: the powers t^1..t^M by a running product feed S_1..S_M and
+    // T_0..T_M; each higher sum S_k, k = M+1..2M, takes the product t^a t^b
+    // (a = k/2, b = k - a <= M) in one fma, with as many roundings as the
+    // running product would give t^k (2k - 1 in both) and M fewer instructions.
+    template <bool FIRST>
+    __device__ __forceinline__ void add_pair_powers(u64 t, u64 y) {
+        u64 pw[M + 1];
+        pw[1] = t;
+#pragma unroll
+        for (int k = 2; k <= M; ++k) pw[k] = mul2(pw[k - 1], t);
+        acc[2 * M] = FIRST ? y : add2(acc[2 * M], y);
+#pragma unroll
+        for (int k = 1; k <= M; ++k) {
+            acc[k - 1] = FIRST ? pw[k] : add2(acc[k - 1], pw[k]);
+            acc[2 * M + k] = FIRST ? mul2(pw[k], y) : fma2(pw[k], y, acc[2 * M + k]);
+        }
+#pragma unroll
+        for (int k = M + 1; k <= 2 * M; ++k) {
+            const int a = k / 2, b = k - k / 2;
+            acc[k - 1] = FIRST ? mul2(pw[a], pw[b]) : fma2(pw[a], pw[b], acc[k - 1]);
         }
     }
 
@@ -328,9 +358,11 @@ struct AccF32 {
     }
 
     // Chebyshev sign of accumulator a: slot a < 2M holds the moment of
-    // degree a + 1, slot 2M + k the right-hand side of degree k.
+    // degree a + 1 (for a degree k > M the product sum of v_a v_b, sign
+    // sigma_a sigma_b), slot 2M + k the right-hand side of degree k.
     static __device__ __forceinline__ bool negated(int a) {
         const int k = a < 2 * M ? a + 1 : a - 2 * M;
+        if (CHEB && a < 2 * M && k > M) return ((k / 2) & 2) != ((k - k / 2) & 2);
         return CHEB && (k & 2);
     }
 
@@ -372,23 +404,24 @@ struct AccF64 {
 #pragma unroll
         for (int a = 0; a < N; ++a) acc[a] = 0.0;
     }
+    // Basis values phi_1..phi_M (powers, or T_k by the recurrence) feed the
+    // sums of degree 1..M; the slot of degree k = M+1..2M takes phi_a phi_b
+    // (a = k/2, b = k - a): the power t^k itself, or for the Chebyshev basis
+    // (C_k + C_{b-a}) / 2, turned into C_k by cheb_moments_from_products().
     __device__ __forceinline__ void add_point(double t, double y) {
-        double p = t, pm1 = 1.0;
-        acc[2 * M] += y;
-        acc[0] += p;
-        acc[2 * M + 1] = fma(p, y, acc[2 * M + 1]);
+        double v[M + 1];
+        v[0] = 1.0;
+        v[1] = t;
 #pragma unroll
-        for (int k = 2; k <= 2 * M; ++k) {
-            if (CHEB) {
-                const double pk = fma(t + t, p, -pm1);
-                pm1 = p;
-                p = pk;
-            } else {
-                p *= t;
-            }
-            acc[k - 1] += p;
-            if (k <= M) acc[2 * M + k] = fma(p, y, acc[2 * M + k]);
+        for (int k = 2; k <= M; ++k) v[k] = CHEB ? fma(t + t, v[k - 1], -v[k - 2]) : v[k - 1] * t;
+        acc[2 * M] += y;
+#pragma unroll
+        for (int k = 1; k <= M; ++k) {
+            acc[k - 1] += v[k];
+            acc[2 * M + k] = fma(v[k], y, acc[2 * M + k]);
         }
+#pragma unroll
+        for (int k = M + 1; k <= 2 * M; ++k) acc[k - 1] = fma(v[k / 2], v[k - k / 2], acc[k - 1]);
     }
 };
 
@@ -520,6 +553,15 @@ __device__ __forceinline__ void block_reduce_d(GetF get, double* red, double* ou
         }
         __syncthreads();
     }
+}
+
+// Chebyshev moments C_k = sum T_k(t) of degree k = m+1..2m from the product
+// sums P_k = sum T_a(t) T_b(t), a = k/2, b = k - a, that the accumulators keep
+// for those degrees: T_a T_b = (T_k + T_{b-a}) / 2 gives C_k = 2 P_k - C_{b-a},
+// with b - a = 0 (C_0: the point count, or the weight sum) or 1.  mo[0..2m]
+// holds C_0, the moments up to degree m and the product sums above.
+__host__ __device__ __forceinline__ void cheb_moments_from_products(int m, double* mo) {
+    for (int k = m + 1; k <= 2 * m; ++k) mo[k] = 2.0 * mo[k] - mo[(k - k / 2) - k / 2];
 }
 
 // ---------------------------------------------------------------------------

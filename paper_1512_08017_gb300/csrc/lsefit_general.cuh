@@ -62,6 +62,10 @@ struct AccGenF32 {
     // instead of adding (the first pair of a compensated batch).
     template <bool FIRST>
     __device__ __forceinline__ void add_pair(u64 t, u64 y, u64 w) {
+        if (!W) {
+            add_pair_unweighted<FIRST>(t, y, w);
+            return;
+        }
         if (W) {
             put<FIRST>(0, w);
             put_fma<FIRST>(2 * M + 1, w, y);
@@ -85,6 +89,31 @@ struct AccGenF32 {
         }
     }
 
+    // Without weights: the basis values phi_1..phi_M (v_k = sigma_k T_k for
+    // the Chebyshev basis, seeded by `seed`, 1 per point and 0 for an empty
+    // lane) feed the moments of degree 1..M and the right-hand sides; the slot
+    // of degree k = M+1..2M takes v_a v_b (a = k/2, b = k - a): t^k for the
+    // monomials, sigma_a sigma_b (C_k + C_{b-a}) / 2 for the Chebyshev basis
+    // (result() removes the sign, cheb_moments_from_products() gives C_k).
+    template <bool FIRST>
+    __device__ __forceinline__ void add_pair_unweighted(u64 t, u64 y, u64 seed) {
+        u64 v[M + 1];
+        v[0] = seed;
+        v[1] = t;
+        const u64 t2 = CHEB ? add2(t, t) : 0ull;
+        const u64 nt2 = CHEB ? mul2(t, pk2(-2.0f, -2.0f)) : 0ull;
+#pragma unroll
+        for (int k = 2; k <= M; ++k) v[k] = CHEB ? fma2((k & 1) ? t2 : nt2, v[k - 1], v[k - 2]) : mul2(v[k - 1], t);
+        put<FIRST>(2 * M + 1, y);
+#pragma unroll
+        for (int k = 1; k <= M; ++k) {
+            put<FIRST>(k, v[k]);
+            put_fma<FIRST>(2 * M + 1 + k, v[k], y);
+        }
+#pragma unroll
+        for (int k = M + 1; k <= 2 * M; ++k) put_fma<FIRST>(k, v[k / 2], v[k - k / 2]);
+    }
+
     // Compensated mode: move the batch sums into the (hi, lo) pairs (TwoSum).
     __device__ __forceinline__ void fold() {
         if (COMP) {
@@ -104,6 +133,7 @@ struct AccGenF32 {
     // the sign its Chebyshev sums carry.
     static __device__ __forceinline__ bool negated(int a) {
         const int k = a <= 2 * M ? a : a - (2 * M + 1);
+        if (CHEB && !W && a <= 2 * M && k > M) return ((k / 2) & 2) != ((k - k / 2) & 2);
         return CHEB && (k & 2);
     }
 
@@ -145,6 +175,23 @@ struct AccGenF64 {
         for (int a = 0; a < N; ++a) acc[a] = 0.0;
     }
     __device__ __forceinline__ void add_point(double t, double y, double w) {
+        if (!W) {
+            // as AccGenF32::add_pair_unweighted: products for the degrees above M
+            double v[M + 1];
+            v[0] = 1.0;
+            v[1] = t;
+#pragma unroll
+            for (int k = 2; k <= M; ++k) v[k] = CHEB ? fma(t + t, v[k - 1], -v[k - 2]) : v[k - 1] * t;
+            acc[2 * M + 1] += y;
+#pragma unroll
+            for (int k = 1; k <= M; ++k) {
+                acc[k] += v[k];
+                acc[2 * M + 1 + k] = fma(v[k], y, acc[2 * M + 1 + k]);
+            }
+#pragma unroll
+            for (int k = M + 1; k <= 2 * M; ++k) acc[k] = fma(v[k / 2], v[k - k / 2], acc[k]);
+            return;
+        }
         if (W) {
             acc[0] += w;
             acc[2 * M + 1] = fma(w, y, acc[2 * M + 1]);
@@ -354,8 +401,12 @@ __device__ void gen_publish(const GenParams& p, const double* blk, bool map_ok, 
         for (int j = 0; j < J; ++j) tot += comb[tid * J + j];
         if (tid == 0 && !W) tot = (double)p.n;
         tot_s[tid] = map_ok ? tot : qnan;
-        if (p.sums) p.sums[tid] = map_ok ? tot : qnan;
     }
+    __syncthreads();
+    // without weights, degrees M+1..2M were accumulated as product sums
+    if (CHEB && !W && tid == 0) cheb_moments_from_products(M, tot_s);
+    __syncthreads();
+    if (tid < N && p.sums) p.sums[tid] = tot_s[tid];
     if (tid == 0) {
         if (p.map_out) {
             p.map_out[0] = map_ok ? c : qnan;

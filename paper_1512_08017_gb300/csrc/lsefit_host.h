@@ -31,4 +31,24 @@ inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_
 
 inline int elem_size(int dtype) { return dtype == 0 ? 8 : (dtype == 1 ? 4 : 2); }
 
+// Launch of a kernel that may start before the kernel ahead of it on the
+// stream has finished (programmatic dependent launch): the kernel must call
+// griddep_wait() before it reads anything its predecessor writes.  Inside a
+// CUDA graph capture the dependency becomes a programmatic graph edge.
+template <typename... Params, typename... Args>
+inline cudaError_t launch_after_prior(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem,
+                                      cudaStream_t stream, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 }  // namespace lsefit
