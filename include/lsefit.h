@@ -70,7 +70,9 @@ enum {
     LSEFIT_ERR_WORKSPACE = 6,     /* host: workspace or plan buffer too small / misaligned */
     LSEFIT_ERR_CUDA = 7,          /* host: a CUDA runtime call or launch failed */
     LSEFIT_ERR_UNSUPPORTED = 8,   /* host: dtype/accum combination not provided */
-    LSEFIT_ERR_SCRATCH_LIMIT = 9  /* host: request exceeds the static scratch of lsefit_fit_noalloc */
+    LSEFIT_ERR_SCRATCH_LIMIT = 9, /* host: request exceeds the static scratch of lsefit_fit_noalloc */
+    LSEFIT_ERR_TIMEOUT = 10       /* per fit (batched): a bounded on-GPU wait for queue space ran out
+                                     (the series is not fitted); not expected in normal operation */
 };
 
 /* Storage type of x and y. */
@@ -556,6 +558,20 @@ size_t lsefit_backward_workspace_size(const lsefit_plan* plan);
 int lsefit_backward(const lsefit_batch* batch, const lsefit_plan* plan, const double* sums,
                     const double* Xt, const double* map, const double* gX, void* dx, void* dy,
                     int32_t* status, void* workspace, size_t workspace_bytes, lsefit_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Diagnostics
+ * ------------------------------------------------------------------------ */
+
+/*
+ * lsefit_check_reciprocal -- out[i] = the reciprocal 1/a[i] exactly as the
+ * Gaussian eliminations and Cholesky factorisations of this library form it
+ * (Newton-Raphson refinement of an FP32 seed; within about an ulp of the
+ * IEEE quotient, not always correctly rounded).  Not in the paper; exposed so
+ * that tests can hold it to its error bound.
+ *  a, out  device double[n]; n >= 0.
+ */
+int lsefit_check_reciprocal(const double* a, double* out, int64_t n, lsefit_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -599,6 +599,34 @@ __device__ __forceinline__ unsigned long long max_abs_bits(unsigned long long ac
     return b > acc ? b : acc;
 }
 
+// 1/a for the eliminations: Newton-Raphson refinement of an approximate
+// reciprocal (r <- r + r (1 - a r), each step squaring the relative error;
+// see e.g. Muller et al., Handbook of Floating-Point Arithmetic, on Newton
+// iterations for the reciprocal).  The seed is the FP32 hardware
+// approximation for a's significand m in [1, 2), about 2^-22 relative; two
+// steps (four FP64 fmas) bring it to the rounding level of FP64 (within an
+// ulp or two; not always correctly rounded).  The exponent goes back by
+// integer arithmetic.  On GB300 an FP64 instruction costs a warp about 64
+// cycles, FP32 instructions and conversions one or two, so this takes about
+// two thirds of the time of IEEE division.  Zero, subnormal, infinite and NaN
+// pivots and |a| >= 2^1022 (met only by singular or overflowing systems)
+// take IEEE division.
+__device__ __forceinline__ double recip_f64(double a) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
+    const int ex = (int)((bits >> 52) & 0x7ffu);
+    if (ex == 0 || ex > 2044) return 1.0 / a;
+    const double m = __longlong_as_double((long long)((bits & 0x800fffffffffffffull) | 0x3ff0000000000000ull));
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__double2float_rn(m)));
+    double r = (double)rf;
+    double e = fma(-m, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-m, r, 1.0);
+    r = fma(r, e, r);
+    // 1/a = r 2^(1023 - ex), r in [0.5, 1]: shift r's exponent field
+    return __longlong_as_double(__double_as_longlong(r) + ((long long)(1023 - ex) << 52));
+}
+
 // Gaussian elimination with partial pivoting of the padded system A z = r
 // (A[.][N] holds r; rows and columns beyond m are the identity), then back
 // substitution.  The pivot is the first row of largest |a_rk|; a pivot of a
@@ -621,7 +649,8 @@ __device__ __forceinline__ int ge_padded(int m, double (&A)[NMAX + 1][NMAX + 2],
                 p = r;
             }
         }
-        if (k <= m && !(__longlong_as_double((long long)best) > tol)) st = LSEFIT_ERR_SINGULAR;
+        // best <= tol, compared on the integer pipe (tol is finite and >= 0)
+        if (k <= m && !(best > (unsigned long long)__double_as_longlong(tol))) st = LSEFIT_ERR_SINGULAR;
 #pragma unroll
         for (int r = k + 1; r < N; ++r) {
             if (r == p) {
@@ -633,7 +662,7 @@ __device__ __forceinline__ int ge_padded(int m, double (&A)[NMAX + 1][NMAX + 2],
                 }
             }
         }
-        const double inv = 1.0 / A[k][k];
+        const double inv = recip_f64(A[k][k]);
         inv_piv[k] = inv;
 #pragma unroll
         for (int r = k + 1; r < N; ++r) {
@@ -702,7 +731,7 @@ __device__ __forceinline__ int hankel_cholesky(int m, const double* S, const dou
         if (j <= m && !(d > tol)) st = LSEFIT_ERR_SINGULAR;
         const double ljj = sqrt(fmax(d, 0.0));
         Lm[j][j] = ljj;
-        inv[j] = 1.0 / ljj;
+        inv[j] = recip_f64(ljj);
 #pragma unroll
         for (int i = j + 1; i < N; ++i) {
             double v = (i <= m && j <= m) ? S[i + j] : 0.0;

@@ -62,3 +62,23 @@ extern "C" int lsefit_solve_cholesky(const double* sums, int64_t count, int m_su
                                      lsefit_stream_t stream) {
     return launch_solve(true, sums, count, m_sums, m, accum, map, X, Xt, status, stream);
 }
+
+// ---------------------------------------------------------------------------
+// Diagnostic: the eliminations' reciprocal on a caller's values (for tests).
+// ---------------------------------------------------------------------------
+namespace lsefit {
+__global__ void reciprocal_kernel(const double* a, double* out, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = recip_f64(a[i]);
+}
+}  // namespace lsefit
+
+extern "C" int lsefit_check_reciprocal(const double* a, double* out, int64_t n, lsefit_stream_t stream) {
+    if (n < 0 || (n > 0 && (a == nullptr || out == nullptr))) return LSEFIT_ERR_INVALID_ARG;
+    if (n == 0) return LSEFIT_OK;
+    const int threads = 256;
+    const int64_t blocks = (n + threads - 1) / threads;
+    if (blocks > 0x7fffffffll) return LSEFIT_ERR_INVALID_ARG;
+    reciprocal_kernel<<<(unsigned)blocks, threads, 0, (cudaStream_t)stream>>>(a, out, n);
+    return cudaGetLastError() == cudaSuccess ? LSEFIT_OK : LSEFIT_ERR_CUDA;
+}

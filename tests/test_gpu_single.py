@@ -342,3 +342,32 @@ def test_full_size_bench_call(L):
         assert abs(sums[k] - S[k]) <= gates.sums_bound(k, Sa[k], batch=8), k
     for k in range(4):
         assert abs(sums[7 + k] - T[k]) <= gates.sums_bound(k + 1, Ta[k], batch=8), k
+
+
+# --- the eliminations' reciprocal -------------------------------------------------------
+
+def test_reciprocal_within_two_ulp_of_ieee_division(L):
+    """The pivots' reciprocal (Newton-Raphson refinement of an FP32 seed) against
+    IEEE division on the GPU: within 2 ulp over magnitudes from 2^-1021 to 2^1021,
+    both signs; zero, infinities and NaN as IEEE division gives them."""
+    from paper_1512_08017_gb300 import lsefit as B
+    rng = np.random.default_rng(123)
+    mant = rng.uniform(1.0, 2.0, 200_000)
+    ex = rng.integers(-1021, 1021, mant.size)
+    a = np.ldexp(mant, ex) * rng.choice([-1.0, 1.0], mant.size)
+    a = np.concatenate([a, [1.0, 2.0, 1.5, np.nextafter(2.0, 0.0), 3.0, 0.1, -7.0, 1e300, -1e-300]])
+    ad = torch.from_numpy(a).cuda()
+    out = torch.empty_like(ad)
+    assert B.lib.lsefit_check_reciprocal(B._ptr(ad), B._ptr(out), a.size, None) == B.OK
+    ref = (1.0 / ad).cpu().numpy()
+    got = out.cpu().numpy()
+    ulp = np.spacing(np.abs(ref))
+    assert np.max(np.abs(got - ref) / ulp) <= 2.0
+    special = torch.tensor([0.0, -0.0, np.inf, -np.inf, np.nan, 5e-324, 2.0 ** 1023], dtype=torch.float64).cuda()
+    so = torch.empty_like(special)
+    assert B.lib.lsefit_check_reciprocal(B._ptr(special), B._ptr(so), special.numel(), None) == B.OK
+    sr = (1.0 / special).cpu().numpy()
+    sg = so.cpu().numpy()
+    assert np.array_equal(np.isnan(sg), np.isnan(sr))
+    fin = ~np.isnan(sr)
+    assert np.array_equal(sg[fin], sr[fin])
