@@ -70,9 +70,7 @@ enum {
     LSEFIT_ERR_WORKSPACE = 6,     /* host: workspace or plan buffer too small / misaligned */
     LSEFIT_ERR_CUDA = 7,          /* host: a CUDA runtime call or launch failed */
     LSEFIT_ERR_UNSUPPORTED = 8,   /* host: dtype/accum combination not provided */
-    LSEFIT_ERR_SCRATCH_LIMIT = 9, /* host: request exceeds the static scratch of lsefit_fit_noalloc */
-    LSEFIT_ERR_TIMEOUT = 10       /* per fit (batched): a bounded on-GPU wait for queue space ran out
-                                     (the series is not fitted); not expected in normal operation */
+    LSEFIT_ERR_SCRATCH_LIMIT = 9  /* host: request exceeds the static scratch of lsefit_fit_noalloc */
 };
 
 /* Storage type of x and y. */

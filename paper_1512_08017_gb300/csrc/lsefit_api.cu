@@ -69,7 +69,6 @@ extern "C" const char* lsefit_status_string(int code) {
         case LSEFIT_ERR_CUDA: return "CUDA error";
         case LSEFIT_ERR_UNSUPPORTED: return "unsupported dtype/accumulation";
         case LSEFIT_ERR_SCRATCH_LIMIT: return "request exceeds the static scratch of lsefit_fit_noalloc";
-        case LSEFIT_ERR_TIMEOUT: return "a bounded on-GPU wait ran out";
         default: return "unknown status";
     }
 }

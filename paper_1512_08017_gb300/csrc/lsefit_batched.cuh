@@ -121,35 +121,33 @@ __device__ __forceinline__ bool load_map_f64(const BParams& p, int64_t s, double
 }
 
 // ---------------------------------------------------------------------------
-// The block's queue of finished series (in the workspace).
+// queue of finished series (per warp, shared memory)
 // row: word 0 = point count (int64 bits), words 1..3m+1 = accumulator totals
 // (double-float pairs, or doubles for FP64 accumulation)
-//
-// Series finished by any warp of the block (or by the whole block in a block
-// task) take consecutive slots.  Slot i is row i mod 32 of region
-// (i / 32) mod 16: batch b = i / 32 fills region b mod 16.  The writer whose
-// row completes a batch of 32 solves it at once, one series per lane, so the
-// FP64 solves overlap the other warps' streaming instead of piling up at the
-// end; only the last, partial batch is solved after the stream.  A region is
-// written by its next batch (b + 16) only once the solver of batch b has
-// loaded its rows into registers: a bounded wait that, if it ever ran out,
-// would give that one series the status LSEFIT_ERR_TIMEOUT.
 // ---------------------------------------------------------------------------
 template <int NMAX>
 struct PendLayout {
     static constexpr int kStride = 3 * NMAX + 2;
-    // per region, in the workspace: rows [32][kStride] words, then sid[32], meta[32]
+    // per warp, in the workspace: rows [32][kStride] words, then sid[32], meta[32]
     static constexpr size_t kWarpBytes = (size_t)32 * kStride * 8 + 32 * 4 * 2;
 };
 
-constexpr int kQRegions = kBWarps;             // regions of 32 rows per block (the workspace holds 16)
-constexpr int kQueueSpin = 1 << 20;            // bounded wait for a region: about 0.1 s with back-off
-
-struct BlockQueue {
-    unsigned char* base;  // the block's kQRegions regions (PendLayout<NMAX>::kWarpBytes each)
-    int* claim;           // shared: slots claimed so far
-    int* fill;            // shared [kQRegions]: rows written in the region's current batch
-    int* loaded;          // shared [kQRegions]: batches of the region loaded by their solvers
+// A warp's queue of finished series.  The entry count n is warp-uniform
+// register state, updated identically by every lane of the owning warp (no
+// lane ever waits on another lane's store to learn it); it is published to
+// shared memory only for the block's final consolidated solve.
+template <int NMAX>
+struct Pend {
+    unsigned long long* row;  // [32][kStride] 8-byte words (global workspace)
+    int* sid;                 // [32] series id (global workspace)
+    int* meta;                // [32] degree (global workspace)
+    int n;                    // entries queued
+    __device__ __forceinline__ void bind(unsigned char* base) {
+        row = reinterpret_cast<unsigned long long*>(base);
+        sid = reinterpret_cast<int*>(base + 32 * PendLayout<NMAX>::kStride * 8);
+        meta = sid + 32;
+        n = 0;
+    }
 };
 
 __device__ __forceinline__ unsigned long long df_bits(dflt v) {
@@ -192,15 +190,14 @@ struct __align__(16) StageRec {
 constexpr int kRingWarpBytes = 2 * kRing * kStageBytes + kRing * (int)sizeof(StageRec);
 
 // Shared memory: [block-reduction scratch | warp rings] (phases 1 and 2 never
-// overlap), blk and comb; the queue of finished series lives in the
-// workspace (written and read once per series), its counters in static
-// shared memory.
+// overlap), blk, comb and the queue counts; the queues of finished series
+// live in the workspace (written and read once per series).
 constexpr size_t kRedBytes = (size_t)kBWarps * kBBlock * 8;
 constexpr size_t kRingsBytes = (size_t)kBWarps * kRingWarpBytes;
 constexpr size_t kScratchBytes = kRedBytes > kRingsBytes ? kRedBytes : kRingsBytes;
 
 __host__ __device__ constexpr size_t batched_smem_bytes(int /*nmax*/) {
-    return kScratchBytes + 32 * 8 /* blk */ + 32 * 8 /* comb */;
+    return kScratchBytes + 32 * 8 /* blk */ + 32 * 8 /* comb */ + kBWarps * 4 /* queue counts */;
 }
 
 __host__ __device__ constexpr size_t pend_warp_bytes(int nmax) {
@@ -468,39 +465,33 @@ __device__ __forceinline__ void ring_wait(int pending) {
     __syncwarp();
 }
 
-// One accumulator word as FP64: a double-float pair or an FP64 value.
-template <int ACC>
-__device__ __forceinline__ double word_to_f64(unsigned long long w) {
-    if (ACC == LSEFIT_ACCUM_F64) return __longlong_as_double((long long)w);
-    const dflt v = bits_df(w);
-    return f32_to_f64_int(v.hi) + f32_to_f64_int(v.lo);
-}
-
-// Solve the queued series in row idx of region r of the block's queue, if
+// Solve one queued series (entry idx of warp ws's queue in this block), if
 // `active`.  Called by all 32 lanes of a warp together (the degree and map
-// votes span the full warp).  The row is loaded into registers first
-// (converted to FP64); with `release` the region is then handed back to the
-// writers of its next batch, before any FP64 work.
+// votes below span the full warp).  Converts the entry's sums to FP64 in place.
 template <int NMAX, int ACC, bool CHEB = false>
-__device__ __noinline__ void pend_solve_slot(const BParams& p, const BlockQueue& q, int r, int idx, bool active,
-                                             bool release) {
+__device__ __noinline__ void pend_solve_entry(const BParams& p, unsigned char* pend_block, int ws, int idx,
+                                              bool active) {
     constexpr int W = PendLayout<NMAX>::kStride;
-    const unsigned char* base = q.base + (size_t)r * PendLayout<NMAX>::kWarpBytes;
-    const unsigned long long* row = reinterpret_cast<const unsigned long long*>(base) + (size_t)idx * W;
-    const int* sid = reinterpret_cast<const int*>(base + 32 * W * 8);
     int m = 0;
     int64_t s = 0;
-    double S[2 * NMAX + 1], T[NMAX + 1];
     double c = 0.0, sc = 1.0;
     bool ok = false;
+    double* sm = nullptr;
     if (active) {
+        unsigned char* base = pend_block + (size_t)ws * PendLayout<NMAX>::kWarpBytes;
+        unsigned long long* row = reinterpret_cast<unsigned long long*>(base) + (size_t)idx * W;
+        const int* sid = reinterpret_cast<const int*>(base + 32 * W * 8);
         m = sid[32 + idx];
         s = sid[idx];
-        S[0] = (double)(long long)row[0];
-#pragma unroll
-        for (int k = 1; k <= 2 * NMAX; ++k) S[k] = k <= 2 * m ? word_to_f64<ACC>(row[k]) : 0.0;
-#pragma unroll
-        for (int j = 0; j <= NMAX; ++j) T[j] = j <= m ? word_to_f64<ACC>(row[2 * m + 1 + j]) : 0.0;
+        const int ns = 3 * m + 2;
+        sm = reinterpret_cast<double*>(row);
+        sm[0] = (double)(long long)row[0];
+        if (ACC != LSEFIT_ACCUM_F64) {
+            for (int k = 1; k < ns; ++k) {
+                const dflt v = bits_df(row[k]);
+                sm[k] = f32_to_f64_int(v.hi) + f32_to_f64_int(v.lo);
+            }
+        }
         if (ACC == LSEFIT_ACCUM_F64) {
             ok = load_map_f64(p, s, c, sc);
         } else {
@@ -509,18 +500,6 @@ __device__ __noinline__ void pend_solve_slot(const BParams& p, const BlockQueue&
             c = f32_to_f64_int(cf);
             sc = f32_to_f64_int(sf);
         }
-    }
-    __syncwarp();
-    if (release && (threadIdx.x & 31) == 0) {
-        q.fill[r] = 0;
-        __threadfence_block();
-        atomicAdd(&q.loaded[r], 1);
-    }
-    if (CHEB && active) {
-        // degrees m+1..2m were accumulated as product sums (cheb_moments_from_products)
-#pragma unroll
-        for (int k = 2; k <= 2 * NMAX; ++k)
-            if (k > m && k <= 2 * m) S[k] = 2.0 * S[k] - S[(k - k / 2) - k / 2];
     }
     // the solve is sized for the largest degree among the lanes solving together
     // (FP64 instructions cost the same for 1 or 32 lanes; padding does not), and
@@ -532,43 +511,45 @@ __device__ __noinline__ void pend_solve_slot(const BParams& p, const BlockQueue&
     const int nc = p.m_max + 1;
     double* xt = p.Xt ? p.Xt + s * nc : nullptr;
     double* x = p.X + s * nc;
+    const double* T = sm + 2 * m + 1;
     int st;
+    if (CHEB && active) cheb_moments_from_products(m, sm);  // degrees m+1..2m were kept as product sums
     if (CHEB) {
-        // Chebyshev basis: G from the moments (S[0] = n), Xt holds the Chebyshev coefficients
+        // Chebyshev basis: G from the moments (sm[0] = n), Xt holds the Chebyshev coefficients
         switch (mw) {
-            case 1: st = solve_general_rt<1, true>(m, S, T, S[0], c, sc, ok, p.eps, xt, x, nc); break;
-            case 2: st = solve_general_rt<2, true>(m, S, T, S[0], c, sc, ok, p.eps, xt, x, nc); break;
-            case 3: st = solve_general_rt<3, true>(m, S, T, S[0], c, sc, ok, p.eps, xt, x, nc); break;
-            case 4: st = solve_general_rt<4, true>(m, S, T, S[0], c, sc, ok, p.eps, xt, x, nc); break;
+            case 1: st = solve_general_rt<1, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc); break;
+            case 2: st = solve_general_rt<2, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc); break;
+            case 3: st = solve_general_rt<3, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc); break;
+            case 4: st = solve_general_rt<4, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc); break;
             default:
                 if constexpr (NMAX > 5) {
                     switch (mw) {
-                        case 5: st = solve_general_rt<5, true>(m, S, T, S[0], c, sc, ok, p.eps, xt, x, nc); break;
-                        case 6: st = solve_general_rt<6, true>(m, S, T, S[0], c, sc, ok, p.eps, xt, x, nc); break;
-                        case 7: st = solve_general_rt<7, true>(m, S, T, S[0], c, sc, ok, p.eps, xt, x, nc); break;
-                        default: st = solve_general_rt<8, true>(m, S, T, S[0], c, sc, ok, p.eps, xt, x, nc); break;
+                        case 5: st = solve_general_rt<5, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc); break;
+                        case 6: st = solve_general_rt<6, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc); break;
+                        case 7: st = solve_general_rt<7, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc); break;
+                        default: st = solve_general_rt<8, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc); break;
                     }
                 } else {
-                    st = solve_general_rt<5, true>(m, S, T, S[0], c, sc, ok, p.eps, xt, x, nc);
+                    st = solve_general_rt<5, true>(m, sm, T, sm[0], c, sc, ok, p.eps, xt, x, nc);
                 }
                 break;
         }
     } else
     switch (mw) {
-        case 1: st = solve_hankel_rt<1>(m, S, T, c, sc, ok, p.eps, xt, x, nc, id); break;
-        case 2: st = solve_hankel_rt<2>(m, S, T, c, sc, ok, p.eps, xt, x, nc, id); break;
-        case 3: st = solve_hankel_rt<3>(m, S, T, c, sc, ok, p.eps, xt, x, nc, id); break;
-        case 4: st = solve_hankel_rt<4>(m, S, T, c, sc, ok, p.eps, xt, x, nc, id); break;
+        case 1: st = solve_hankel_rt<1>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
+        case 2: st = solve_hankel_rt<2>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
+        case 3: st = solve_hankel_rt<3>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
+        case 4: st = solve_hankel_rt<4>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
         default:
             if constexpr (NMAX > 5) {
                 switch (mw) {
-                    case 5: st = solve_hankel_rt<5>(m, S, T, c, sc, ok, p.eps, xt, x, nc, id); break;
-                    case 6: st = solve_hankel_rt<6>(m, S, T, c, sc, ok, p.eps, xt, x, nc, id); break;
-                    case 7: st = solve_hankel_rt<7>(m, S, T, c, sc, ok, p.eps, xt, x, nc, id); break;
-                    default: st = solve_hankel_rt<8>(m, S, T, c, sc, ok, p.eps, xt, x, nc, id); break;
+                    case 5: st = solve_hankel_rt<5>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
+                    case 6: st = solve_hankel_rt<6>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
+                    case 7: st = solve_hankel_rt<7>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
+                    default: st = solve_hankel_rt<8>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id); break;
                 }
             } else {
-                st = solve_hankel_rt<5>(m, S, T, c, sc, ok, p.eps, xt, x, nc, id);
+                st = solve_hankel_rt<5>(m, sm, T, c, sc, ok, p.eps, xt, x, nc, id);
             }
             break;
     }
@@ -576,95 +557,37 @@ __device__ __noinline__ void pend_solve_slot(const BParams& p, const BlockQueue&
     if (p.sums) {
         const double qnan = __longlong_as_double(0x7ff8000000000000ll);
         const int stride = 3 * p.m_max + 2;
+        const int ns = 3 * m + 2;
         double* out = p.sums + s * stride;
-#pragma unroll
-        for (int k = 0; k <= 2 * NMAX; ++k)
-            if (k <= 2 * m) out[k] = ok ? S[k] : qnan;
-#pragma unroll
-        for (int j = 0; j <= NMAX; ++j)
-            if (j <= m) out[2 * m + 1 + j] = ok ? T[j] : qnan;
-        for (int k = 3 * m + 2; k < stride; ++k) out[k] = 0.0;
+        for (int k = 0; k < stride; ++k) out[k] = k < ns ? (ok ? sm[k] : qnan) : 0.0;
     }
 }
 
-// Claims the next slot of the block's queue for the calling warp (all lanes;
-// the slot is returned to every lane) and waits, bounded, until the slot's
-// region has been released by the solver of its previous batch.  ok = false
-// when that wait ran out.
-__device__ __forceinline__ int bq_claim_warp(const BlockQueue& q, bool& ok) {
+// The warp solves its full queue (32 series), one per lane, and empties it.
+template <int NMAX, int ACC, bool CHEB = false>
+__device__ __forceinline__ void pend_solve(const BParams& p, Pend<NMAX>& q) {
+    __syncwarp();
     const int lane = threadIdx.x & 31;
-    int slot = 0, ready = 1;
-    if (lane == 0) {
-        slot = atomicAdd(q.claim, 1);
-        const int gen = (slot >> 5) / kQRegions;
-        if (gen > 0) {
-            const int r = (slot >> 5) & (kQRegions - 1);
-            ready = 0;
-            for (int it = 0; it < kQueueSpin; ++it) {
-                if (*(volatile int*)&q.loaded[r] >= gen) {
-                    ready = 1;
-                    break;
-                }
-                __nanosleep(64);
-            }
-            __threadfence_block();
-        }
-    }
-    slot = __shfl_sync(0xffffffffu, slot, 0);
-    ok = __shfl_sync(0xffffffffu, ready, 0) != 0;
-    return slot;
+    unsigned char* base = reinterpret_cast<unsigned char*>(q.row);
+    // the queue of warp w of this block is at pend_block + w * kWarpBytes; solve
+    // entries relative to this warp's own queue
+    pend_solve_entry<NMAX, ACC, CHEB>(p, base, 0, lane, lane < q.n);
+    __syncwarp();
+    q.n = 0;
 }
 
-// Status and NaN row of series s, which is not fitted (code: why).
-__device__ __forceinline__ void mark_unfitted(const BParams& p, int64_t s, int code) {
+// Status and NaN row of a series that is not fitted at all (bad degree).
+__device__ __forceinline__ void mark_invalid(const BParams& p, int64_t s) {
     const int nc = p.m_max + 1;
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
     for (int i = 0; i < nc; ++i) {
         p.X[s * nc + i] = qnan;
         if (p.Xt) p.Xt[s * nc + i] = qnan;
     }
-    if (p.sums)
+    if (p.sums) {
         for (int k = 0; k < 3 * p.m_max + 2; ++k) p.sums[s * (3 * p.m_max + 2) + k] = qnan;
-    p.status[s] = code;
-}
-
-// A warp queues its finished series s (degree M, `count` points; lane l < nw
-// holds accumulator word l) and, if its row completes a batch, solves the batch.
-template <int NMAX, int ACC, bool CHEB>
-__device__ __forceinline__ void bq_push_warp(const BParams& p, const BlockQueue& q, int64_t s, int M,
-                                             long long count, unsigned long long word, int nw) {
-    constexpr int W = PendLayout<NMAX>::kStride;
-    const int lane = threadIdx.x & 31;
-    bool ok;
-    const int slot = bq_claim_warp(q, ok);
-    const int r = (slot >> 5) & (kQRegions - 1), idx = slot & 31;
-    if (!ok) {  // this row is not written: its batch is finished after the stream
-        if (lane == 0) mark_unfitted(p, s, LSEFIT_ERR_TIMEOUT);
-        return;
     }
-    unsigned char* base = q.base + (size_t)r * PendLayout<NMAX>::kWarpBytes;
-    unsigned long long* row = reinterpret_cast<unsigned long long*>(base) + (size_t)idx * W;
-    int* sid = reinterpret_cast<int*>(base + 32 * W * 8);
-    if (lane < nw) row[lane + 1] = word;
-    if (lane == 0) {
-        row[0] = (unsigned long long)count;
-        sid[idx] = (int)s;
-        sid[32 + idx] = M;
-    }
-    __threadfence_block();  // the row before the count that publishes it
-    __syncwarp();
-    int f = 0;
-    if (lane == 0) f = atomicAdd(&q.fill[r], 1);
-    f = __shfl_sync(0xffffffffu, f, 0);
-    if (f == 31) {  // the batch is complete: solve it now
-        __threadfence_block();
-        pend_solve_slot<NMAX, ACC, CHEB>(p, q, r, lane, true, true);
-    }
-}
-
-// Status and NaN row of a series that is not fitted at all (bad degree).
-__device__ __forceinline__ void mark_invalid(const BParams& p, int64_t s) {
-    mark_unfitted(p, s, LSEFIT_ERR_INVALID_ARG);
+    p.status[s] = LSEFIT_ERR_INVALID_ARG;
 }
 
 template <int M>
@@ -677,7 +600,7 @@ struct Unroll {
 // ---------------------------------------------------------------------------
 template <int NMAX, int DT, int ACC, int M, bool CHEB = false>
 __device__ void block_task(const BParams& p, int t, int4 task, dflt* red, double* blk, double* comb,
-                           const BlockQueue& q, int* s_last) {
+                           Pend<NMAX>& q0, int* s_last) {
     constexpr int N = 3 * M + 1;
     const int tid = threadIdx.x;
     const int64_t s = task.x;
@@ -705,10 +628,18 @@ __device__ void block_task(const BParams& p, int t, int4 task, dflt* red, double
             A, p.x, p.y, b, e, tid, kBBlock, c, sc);
         block_reduce_df2<kBBlock, N>([&](int a) { return A.result(a); }, red, reinterpret_cast<dflt*>(blk));
     }
-    // words[0..N-1] now hold this chunk's totals (visible to all threads);
-    // warp 0 queues a finished series
+    // words[0..N-1] now hold this chunk's totals (visible to all threads)
+    const int slot_row = PendLayout<NMAX>::kStride;
     if (nch == 1) {
-        if (tid < 32) bq_push_warp<NMAX, ACC, CHEB>(p, q, s, M, len, tid < N ? words[tid] : 0ull, N);
+        if (tid == 0) {
+            const int slot = q0.n;
+            unsigned long long* row = q0.row + slot * slot_row;
+            row[0] = (unsigned long long)len;
+            for (int a = 0; a < N; ++a) row[a + 1] = words[a];
+            q0.sid[slot] = (int)s;
+            q0.meta[slot] = M;
+        }
+        if (tid < 32) q0.n += 1;
     } else {
         const int stride = 3 * p.m_max + 1;
         if (tid < N) {
@@ -738,11 +669,21 @@ __device__ void block_task(const BParams& p, int t, int4 task, dflt* red, double
                 reinterpret_cast<unsigned long long*>(comb)[tid] = w;
             }
             __syncthreads();
-            if (tid == 0) p.tickets[first] = 0u;
-            if (tid < 32)
-                bq_push_warp<NMAX, ACC, CHEB>(p, q, s, M, len,
-                                              tid < N ? reinterpret_cast<unsigned long long*>(comb)[tid] : 0ull, N);
+            if (tid == 0) {
+                const int slot = q0.n;
+                unsigned long long* row = q0.row + slot * slot_row;
+                row[0] = (unsigned long long)len;
+                for (int a = 0; a < N; ++a) row[a + 1] = reinterpret_cast<unsigned long long*>(comb)[a];
+                q0.sid[slot] = (int)s;
+                q0.meta[slot] = M;
+                p.tickets[first] = 0u;
+            }
+            if (tid < 32) q0.n += 1;
         }
+    }
+    if (tid < 32) {
+        __syncwarp();
+        if (q0.n == 32) pend_solve<NMAX, ACC, CHEB>(p, q0);
     }
 }
 
@@ -834,14 +775,13 @@ __device__ __forceinline__ void stage_accumulate_f64(AccF64<M, CHEB>& A, const u
 // One series streamed through the ring.  On entry the stage at `slot` is its
 // first stage and has landed; on return `slot` is the stage after its last.
 template <int NMAX, int DT, int ACC, int M, bool CHEB = false>
-__device__ void ring_task(const BParams& p, Ring& R, int& slot, int& pending, Cursor& cu, const BlockQueue& q) {
+__device__ void ring_task(const BParams& p, Ring& R, int& slot, int& pending, Cursor& cu, Pend<NMAX>& q) {
     constexpr int N = 3 * M + 1;
     constexpr int NP = N <= 16 ? 16 : 32;
     const int lane = threadIdx.x & 31;
     const int s = R.rec[slot].s;
     const double2 mraw = R.rec[slot].map;
     long long count = 0;
-    unsigned long long word = 0;  // lane l < N: the warp total of accumulator l
     if constexpr (ACC == LSEFIT_ACCUM_F64) {
         const bool ok = !isnan(mraw.x);
         const double c = ok ? mraw.x : 0.0, sc = ok ? mraw.y : 1.0;
@@ -863,7 +803,9 @@ __device__ void ring_task(const BParams& p, Ring& R, int& slot, int& pending, Cu
 #pragma unroll
         for (int a = 0; a < NP; ++a) v[a] = a < N ? A.acc[a] : 0.0;
         const double tot = warp_reduce_scatter_d<NP>(v);
-        word = (unsigned long long)__double_as_longlong(tot);
+        const int qs = q.n;
+        unsigned long long* row = q.row + qs * PendLayout<NMAX>::kStride;
+        if (lane < N) row[lane + 1] = (unsigned long long)__double_as_longlong(tot);
     } else {
         const float2 mf = *reinterpret_cast<const float2*>(&mraw);
         const bool ok = !isnan(mf.x);
@@ -901,14 +843,24 @@ __device__ void ring_task(const BParams& p, Ring& R, int& slot, int& pending, Cu
             }
         }
         const dflt tot = warp_reduce_scatter_df<NP>(v);
-        word = df_bits(tot);
+        const int qs = q.n;
+        unsigned long long* row = q.row + qs * PendLayout<NMAX>::kStride;
+        if (lane < N) row[lane + 1] = df_bits(tot);
     }
-    bq_push_warp<NMAX, ACC, CHEB>(p, q, s, M, count, word, N);
+    if (lane == 0) {
+        const int qs = q.n;
+        q.row[qs * PendLayout<NMAX>::kStride] = (unsigned long long)count;
+        q.sid[qs] = s;
+        q.meta[qs] = M;
+    }
+    q.n += 1;
+    __syncwarp();
+    if (q.n == 32) pend_solve<NMAX, ACC, CHEB>(p, q);
 }
 
 template <int NMAX, int DT, int ACC, bool CHEB = false>
 __device__ __forceinline__ void dispatch_ring(const BParams& p, int m, Ring& R, int& slot, int& pending,
-                                              Cursor& cu, const BlockQueue& q) {
+                                              Cursor& cu, Pend<NMAX>& q) {
     switch (m) {
         case 1: ring_task<NMAX, DT, ACC, 1, CHEB>(p, R, slot, pending, cu, q); break;
         case 2: ring_task<NMAX, DT, ACC, 2, CHEB>(p, R, slot, pending, cu, q); break;
@@ -929,19 +881,19 @@ __device__ __forceinline__ void dispatch_ring(const BParams& p, int m, Ring& R, 
 
 template <int NMAX, int DT, int ACC, bool CHEB = false>
 __device__ __forceinline__ void dispatch_block(const BParams& p, int t, int4 task, int m, dflt* red,
-                                               double* blk, double* comb, const BlockQueue& q, int* s_last) {
+                                               double* blk, double* comb, Pend<NMAX>& q0, int* s_last) {
     switch (m) {
-        case 1: block_task<NMAX, DT, ACC, 1, CHEB>(p, t, task, red, blk, comb, q, s_last); break;
-        case 2: block_task<NMAX, DT, ACC, 2, CHEB>(p, t, task, red, blk, comb, q, s_last); break;
-        case 3: block_task<NMAX, DT, ACC, 3, CHEB>(p, t, task, red, blk, comb, q, s_last); break;
-        case 4: block_task<NMAX, DT, ACC, 4, CHEB>(p, t, task, red, blk, comb, q, s_last); break;
-        case 5: block_task<NMAX, DT, ACC, 5, CHEB>(p, t, task, red, blk, comb, q, s_last); break;
+        case 1: block_task<NMAX, DT, ACC, 1, CHEB>(p, t, task, red, blk, comb, q0, s_last); break;
+        case 2: block_task<NMAX, DT, ACC, 2, CHEB>(p, t, task, red, blk, comb, q0, s_last); break;
+        case 3: block_task<NMAX, DT, ACC, 3, CHEB>(p, t, task, red, blk, comb, q0, s_last); break;
+        case 4: block_task<NMAX, DT, ACC, 4, CHEB>(p, t, task, red, blk, comb, q0, s_last); break;
+        case 5: block_task<NMAX, DT, ACC, 5, CHEB>(p, t, task, red, blk, comb, q0, s_last); break;
         default:
             if constexpr (NMAX > 5) {
                 switch (m) {
-                    case 6: block_task<NMAX, DT, ACC, 6, CHEB>(p, t, task, red, blk, comb, q, s_last); break;
-                    case 7: block_task<NMAX, DT, ACC, 7, CHEB>(p, t, task, red, blk, comb, q, s_last); break;
-                    default: block_task<NMAX, DT, ACC, 8, CHEB>(p, t, task, red, blk, comb, q, s_last); break;
+                    case 6: block_task<NMAX, DT, ACC, 6, CHEB>(p, t, task, red, blk, comb, q0, s_last); break;
+                    case 7: block_task<NMAX, DT, ACC, 7, CHEB>(p, t, task, red, blk, comb, q0, s_last); break;
+                    default: block_task<NMAX, DT, ACC, 8, CHEB>(p, t, task, red, blk, comb, q0, s_last); break;
                 }
             }
             break;
@@ -956,16 +908,13 @@ __global__ void __launch_bounds__(kBBlock, 1) batched_kernel(BParams p) {
     dflt* red = reinterpret_cast<dflt*>(smem);
     double* blk = reinterpret_cast<double*>(smem + kScratchBytes);
     double* comb = blk + 32;
-    __shared__ int s_queue[1 + 2 * kQRegions];  // claim, fill[kQRegions], loaded[kQRegions]
+    int* counts = reinterpret_cast<int*>(comb + 32);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    static_assert(kQRegions == kBWarps, "the workspace holds one region of 32 rows per warp of a block");
-    BlockQueue q;
-    q.base = p.pend + (size_t)blockIdx.x * kQRegions * PendLayout<NMAX>::kWarpBytes;
-    q.claim = s_queue;
-    q.fill = s_queue + 1;
-    q.loaded = s_queue + 1 + kQRegions;
-    if (tid < 1 + 2 * kQRegions) s_queue[tid] = 0;
-    __syncthreads();
+    unsigned char* pend_block = p.pend + (size_t)blockIdx.x * kBWarps * PendLayout<NMAX>::kWarpBytes;
+    // each warp's queue; block tasks queue their series in warp 0's (whose
+    // threads alone touch it there, so its count stays in warp 0's registers)
+    Pend<NMAX> q;
+    q.bind(pend_block + warp * PendLayout<NMAX>::kWarpBytes);
 
     // phase 1: block tasks (their queue counter is cleared by the preparation launch)
     if (p.n_block_tasks > 0) griddep_wait();
@@ -999,18 +948,21 @@ __global__ void __launch_bounds__(kBBlock, 1) batched_kernel(BParams p) {
             dispatch_ring<NMAX, DT, ACC, CHEB>(p, R.rec[slot].deg, R, slot, pending, cu, q);
         }
     }
-    // every completed batch of the queue has been solved by its last writer;
-    // what is left is the last, partial batch (and any batch a timed-out wait
-    // left short): warp w finishes region w
+    // leftover queued series of all warps, solved 32 per warp across the block
+    if (lane == 0) counts[warp] = q.n;
     __syncthreads();
     {
-        const int total = *q.claim;
-        if (total > 0 && warp <= (total - 1) >> 5 && q.fill[warp] > 0) {
-            const int b_last = (total - 1) >> 5;
-            const int b = b_last - ((b_last - warp) & (kQRegions - 1));  // the region's latest batch
-            const int claimed = min(32, total - 32 * b);
-            __syncwarp();
-            pend_solve_slot<NMAX, ACC, CHEB>(p, q, warp, lane, lane < claimed, false);
+        int total = 0;
+        for (int w = 0; w < kBWarps; ++w) total += counts[w];
+        for (int base = warp * 32; base < total; base += kBWarps * 32) {
+            const int g = base + lane;
+            int ws = 0, idx = g;
+            while (ws < kBWarps && idx >= counts[ws]) {
+                idx -= counts[ws];
+                ++ws;
+            }
+            __syncwarp();  // the entry solve votes across the full warp
+            pend_solve_entry<NMAX, ACC, CHEB>(p, pend_block, ws, idx, g < total);
         }
     }
     __syncthreads();

@@ -33,7 +33,6 @@ ERR_WORKSPACE = 6
 ERR_CUDA = 7
 ERR_UNSUPPORTED = 8
 ERR_SCRATCH_LIMIT = 9
-ERR_TIMEOUT = 10
 
 F64, F32, BF16 = 0, 1, 2
 ACCUM = {"naive": 0, "comp": 1, "f64": 2}
@@ -43,8 +42,7 @@ MAX_DEGREE_CHEBYSHEV = 16  # Chebyshev basis with FP64 accumulation
 
 # per-fit status names (same vocabulary as the oracle's)
 STATUS_NAMES = {OK: "ok", ERR_N_TOO_SMALL: "n_too_small", ERR_SINGULAR: "singular",
-                ERR_NONFINITE: "nonfinite", ERR_BAD_INTERVAL: "bad_interval", ERR_INVALID_ARG: "invalid_arg",
-                ERR_TIMEOUT: "timeout"}
+                ERR_NONFINITE: "nonfinite", ERR_BAD_INTERVAL: "bad_interval", ERR_INVALID_ARG: "invalid_arg"}
 
 _DTYPES = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
 
