@@ -251,6 +251,7 @@ struct Cursor {
 };
 
 constexpr int kStaticRounds = 3;
+constexpr int kOwnSolveMin = 16;  // queue entries from which a warp solves its own queue after its stream
 
 // Returns {task index (kNone: no work left), round, queue} for the draw made
 // in state (round, cls).  Out of line, with the state passed by value, so the
@@ -948,6 +949,11 @@ __global__ void __launch_bounds__(kBBlock, 1) batched_kernel(BParams p) {
             dispatch_ring<NMAX, DT, ACC, CHEB>(p, R.rec[slot].deg, R, slot, pending, cu, q);
         }
     }
+    // A warp that ends its stream with a well-filled queue solves it at once,
+    // while the block's other warps are still streaming; the rest of the
+    // block's queued series are solved together after the stream, 32 per warp
+    // (a warp-solve costs the same FP64 instructions for 1 lane as for 32).
+    if (q.n >= kOwnSolveMin) pend_solve<NMAX, ACC, CHEB>(p, q);
     // leftover queued series of all warps, solved 32 per warp across the block
     if (lane == 0) counts[warp] = q.n;
     __syncthreads();

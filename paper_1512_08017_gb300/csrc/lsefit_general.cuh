@@ -31,20 +31,23 @@ namespace lsefit {
 // weight pair, or, without weights, 1 for a point and 0 for an empty lane
 // (it seeds the Chebyshev recurrence, in which an empty lane with t = 0
 // would otherwise give T_2(0) = -1).
+// Compensation (COMP): per slot a scalar TwoSum pair (hi, lo); a batch's two
+// packed lane sums are added in FP32 (one rounding of the batch's own size)
+// and then moved into (hi, lo) exactly.
 template <int M, bool COMP, bool W, bool CHEB>
 struct AccGenF32 {
     static constexpr int N = 3 * M + 2;
     static constexpr int K0 = W ? 0 : 1;
     u64 acc[N];
-    u64 phi[COMP ? N : 1], plo[COMP ? N : 1];
+    float shi[COMP ? N : 1], slo[COMP ? N : 1];
 
     __device__ __forceinline__ void init() {
 #pragma unroll
         for (int a = 0; a < N; ++a) {
             acc[a] = 0ull;
             if (COMP) {
-                phi[a] = 0ull;
-                plo[a] = 0ull;
+                shi[a] = 0.0f;
+                slo[a] = 0.0f;
             }
         }
     }
@@ -119,12 +122,11 @@ struct AccGenF32 {
         if (COMP) {
 #pragma unroll
             for (int a = K0; a < N; ++a) {
-                const u64 b = acc[a];
-                const u64 s = add2(phi[a], b);
-                const u64 bb = sub2(s, phi[a]);
-                const u64 e = add2(sub2(phi[a], sub2(s, bb)), sub2(b, bb));
-                plo[a] = add2(plo[a], e);
-                phi[a] = s;
+                float x0, x1, sh, e;
+                up2(acc[a], x0, x1);
+                two_sum(shi[a], __fadd_rn(x0, x1), sh, e);
+                shi[a] = sh;
+                slo[a] = __fadd_rn(slo[a], e);
             }
         }
     }
@@ -152,11 +154,8 @@ struct AccGenF32 {
             r.hi = 0.0f;
             r.lo = 0.0f;
         } else if (COMP) {
-            float x0, x1, l0, l1;
-            up2(phi[a], x0, x1);
-            up2(plo[a], l0, l1);
-            const dflt u = {x0, l0}, v = {x1, l1};
-            r = df_add(u, v);
+            r.hi = shi[a];
+            r.lo = slo[a];
         } else {
             float x0, x1;
             up2(acc[a], x0, x1);

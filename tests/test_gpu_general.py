@@ -280,3 +280,4 @@ def test_chebyshev_high_degree_limits(L):
         L.fit_general(x, x, 9, basis="monomial", accum="f64")
     with pytest.raises(ValueError):
         L.fit_general(x, x, 17, basis="chebyshev", accum="f64")
+
