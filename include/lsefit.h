@@ -349,6 +349,8 @@ typedef struct lsefit_plan {
                                     (c = the degree, 0 = a degree outside 1..LSEFIT_MAX_DEGREE
                                     or no degrees given) are [class_begin[c], class_begin[c+1]) */
     int64_t class_points[LSEFIT_MAX_DEGREE + 1]; /* schedule 3: points of each class */
+    int64_t warp_task_len;    /* the common length of every warp task, or 0 when they differ
+                                 (lsefit_backward then splits their points evenly over its warps) */
 } lsefit_plan;
 
 /*

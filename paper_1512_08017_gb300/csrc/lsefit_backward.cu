@@ -45,6 +45,7 @@ struct BwParams {
     int n_block_tasks;
     const int4* warp_tasks;  // {series, first point (low, high), length}
     int n_warp_tasks;
+    int64_t warp_task_len;  // common length of the warp tasks, 0 when they differ
     unsigned* counters;     // [0] block queue, [1] warp queue, [2] exited blocks
 };
 
@@ -354,7 +355,27 @@ __global__ void __launch_bounds__(kBwBlock) grad_kernel(BwParams p) {
         grad_dispatch<DT>(p, s, b, e, tid, kBwBlock);
     }
     // warp tasks in reverse plan order: the forward pass read the last tasks of
-    // the plan last, so their points are the ones still held in L2
+    // the plan last, so their points are the ones still held in L2.  Tasks of one
+    // common length are split evenly by points over all warps (numbered
+    // warp-major, so every SM gets the same share), which balances a batch of
+    // fewer tasks than twice the warps; otherwise warps draw whole tasks.
+    if (p.warp_task_len > 0) {
+        const int64_t L = p.warp_task_len;
+        const int64_t total = (int64_t)p.n_warp_tasks * L;
+        const int64_t nw = (int64_t)gridDim.x * (kBwBlock / 32);
+        const int64_t wid = (int64_t)(tid >> 5) * gridDim.x + blockIdx.x;
+        const int64_t per = ((total + nw - 1) / nw + 3) / 4 * 4;  // whole 16-byte vectors of FP32 points
+        int64_t pos = min(total, wid * per);
+        const int64_t hi = min(total, pos + per);
+        while (pos < hi) {
+            const int64_t r = pos / L;                 // r-th task from the end of the plan
+            const int64_t seg = min(hi, (r + 1) * L);  // this task's part of the range
+            const int4 task = p.warp_tasks[p.n_warp_tasks - 1 - r];
+            const int64_t first = ((int64_t)(unsigned)task.z << 32) | (unsigned)task.y;
+            grad_dispatch<DT>(p, task.x, first + (pos - r * L), first + (seg - r * L), lane, 32);
+            pos = seg;
+        }
+    } else
     for (;;) {
         int t = 0;
         if (lane == 0) t = (int)atomicAdd(&p.counters[1], 1u);
@@ -449,6 +470,7 @@ extern "C" int lsefit_backward(const lsefit_batch* batch, const lsefit_plan* pla
     p.n_block_tasks = plan->n_block_tasks;
     p.warp_tasks = reinterpret_cast<const int4*>(plan->warp_tasks);
     p.n_warp_tasks = plan->n_warp_tasks;
+    p.warp_task_len = plan->warp_task_len;
     p.counters = reinterpret_cast<unsigned*>(ws);
     auto gk = b.dtype == LSEFIT_F64 ? grad_kernel<LSEFIT_F64>
               : b.dtype == LSEFIT_F32 ? grad_kernel<LSEFIT_F32> : grad_kernel<LSEFIT_BF16>;

@@ -133,6 +133,12 @@ extern "C" int lsefit_plan_build(const int64_t* offsets, const int32_t* degree, 
             block_tasks[4 * t + 3] = (int32_t)first;
         }
     }
+    plan->warp_task_len = shorts.empty() ? 0 : len_of(shorts[0]);
+    for (int32_t s : shorts)
+        if (len_of(s) != plan->warp_task_len) {
+            plan->warp_task_len = 0;
+            break;
+        }
     for (size_t i = 0; i < shorts.size(); ++i) {
         const int32_t sid = shorts[i];
         const uint64_t b = (uint64_t)offsets[sid];

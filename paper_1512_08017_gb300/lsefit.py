@@ -77,7 +77,7 @@ class Plan(ctypes.Structure):
                 ("tuning", Tuning), ("grid", ctypes.c_int32), ("num_sms", ctypes.c_int32),
                 ("block_tasks", ctypes.c_void_p), ("warp_tasks", ctypes.c_void_p),
                 ("class_begin", ctypes.c_int32 * (MAX_DEGREE + 2)),
-                ("class_points", ctypes.c_int64 * (MAX_DEGREE + 1))]
+                ("class_points", ctypes.c_int64 * (MAX_DEGREE + 1)), ("warp_task_len", ctypes.c_int64)]
 
 
 # (name, restype, argtypes) of every symbol include/lsefit.h declares

@@ -119,3 +119,18 @@ def test_degree_classes_without_degrees(B):
     rc, plan, bt, wt = build(B, off, warp_max_len=1 << 20)
     assert rc == B.OK
     assert list(plan.class_begin) == [0] + [5] * 9 and plan.class_points[0] == lens.sum()
+
+
+
+def test_plan_records_a_common_warp_task_length(B):
+    """warp_task_len: the length every warp task shares (the gradient pass then
+    splits their points evenly over its warps), 0 when lengths differ."""
+    rc, plan, _, _ = build(B, np.arange(0, 65 * 4096, 4096), m_max=3)
+    assert rc == B.OK and plan.warp_task_len == 4096
+    rc, plan, _, _ = build(B, [0, 10, 30, 60], m_max=3)
+    assert rc == B.OK and plan.warp_task_len == 0
+    # series longer than warp_max_len become block tasks and do not count
+    rc, plan, _, _ = build(B, [0, 100, 200, 300, 100300], m_max=3, warp_max_len=1000)
+    assert rc == B.OK and plan.warp_task_len == 100 and plan.n_block_tasks > 0
+    rc, plan, _, _ = build(B, [0], m_max=3)
+    assert rc == B.OK and plan.warp_task_len == 0
