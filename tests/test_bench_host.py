@@ -86,3 +86,29 @@ def test_contract_defaults():
     assert a.gpus == 1 and a.impl == "lsefit" and a.workload == "single_large"
     assert a.warmup >= 3 and a.steps >= 1
     assert a.n == 1 << 28
+
+
+def test_error_helpers():
+    """The coefficient-error helpers of the bench line: the backward error of an
+    exact solution of the normal equations is at rounding level, that of a
+    perturbed one is not; rel_err is the normwise relative error."""
+    import numpy as np
+    S = np.array([4.0, 2.0, 3.0, 2.5, 2.8])  # S_0..S_4 of a degree-2 system
+    A = np.array([[S[j + k] for k in range(3)] for j in range(3)])
+    X = np.array([0.5, -1.0, 2.0])
+    T = A @ X
+    assert bench.backward_err(S, T, 2, X) < 1e-15
+    assert bench.backward_err(S, T, 2, X * (1 + 1e-6)) > 1e-8
+    assert abs(bench.rel_err([1.0, 2.0], [1.0, 2.0])) == 0.0
+    assert abs(bench.rel_err([1.0, 2.1], [1.0, 2.0]) - 0.1 / np.sqrt(5.0)) < 1e-15
+
+
+def test_host_placement_helpers():
+    import numpy as np
+    a = np.ones(1 << 16)
+    node = bench.page_node(a.ctypes.data)
+    assert node is None or node >= 0
+    nodes = bench.numa_nodes_with_cpus()
+    assert isinstance(nodes, dict)
+    for k, v in nodes.items():
+        assert k >= 0 and isinstance(v, str)
