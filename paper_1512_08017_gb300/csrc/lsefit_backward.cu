@@ -335,7 +335,7 @@ __device__ __forceinline__ void grad_dispatch(const BwParams& p, int64_t s, int6
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kBwBlock) grad_kernel(BwParams p) {
+__global__ void __launch_bounds__(kBwBlock) grad_kernel(__grid_constant__ const BwParams p) {
     __shared__ int s_task;
     const int tid = threadIdx.x, lane = tid & 31;
     // lambda, the FP32 copies and the queue counters come from the lambda launch

@@ -79,7 +79,7 @@ struct BParams {
 // different layouts.
 // ---------------------------------------------------------------------------
 template <bool FP32MAP>
-__global__ void batched_prep_kernel(BParams p) {
+__global__ void batched_prep_kernel(__grid_constant__ const BParams p) {
     griddep_launch_dependents();  // the persistent kernel may start its set-up now
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < kCounters) p.counters[s] = 0u;
@@ -902,7 +902,7 @@ __device__ __forceinline__ void dispatch_block(const BParams& p, int t, int4 tas
 }
 
 template <int NMAX, int DT, int ACC, bool CHEB = false>
-__global__ void __launch_bounds__(kBBlock, 1) batched_kernel(BParams p) {
+__global__ void __launch_bounds__(kBBlock, 1) batched_kernel(__grid_constant__ const BParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_task;
     __shared__ int s_last;

@@ -418,7 +418,7 @@ __device__ void gen_publish(const GenParams& p, const double* blk, bool map_ok, 
 }
 
 template <int M, int DT, bool COMP, bool W, bool CHEB, int UNROLL>
-__global__ void __launch_bounds__(kGenBlock, pass_min_blocks<M>()) gen_kernel_f32(GenParams p) {
+__global__ void __launch_bounds__(kGenBlock, pass_min_blocks<M>()) gen_kernel_f32(__grid_constant__ const GenParams p) {
     constexpr int N = 3 * M + 2;
     __shared__ dflt red[(kGenBlock / 32) * kGenBlock];
     __shared__ double blk[N];
@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(kGenBlock, pass_min_blocks<M>()) gen_kernel_f3
 }
 
 template <int M, int DT, bool W, bool CHEB, int UNROLL>
-__global__ void __launch_bounds__(kGenBlock) gen_kernel_f64(GenParams p) {
+__global__ void __launch_bounds__(kGenBlock) gen_kernel_f64(__grid_constant__ const GenParams p) {
     constexpr int N = 3 * M + 2;
     __shared__ double red[(kGenBlock / 32) * kGenBlock];
     __shared__ double blk[N];

@@ -112,7 +112,7 @@ __device__ __forceinline__ void ps_publish(const PSParams& p, const double* blk,
 
 // FP32 / BF16 storage, NAIVE or COMP accumulation.
 template <int M, int DT, bool COMP, bool MAP, int UNROLL>
-__global__ void __launch_bounds__(kPSBlock, pass_min_blocks<M>()) ps_kernel_f32(PSParams p) {
+__global__ void __launch_bounds__(kPSBlock, pass_min_blocks<M>()) ps_kernel_f32(__grid_constant__ const PSParams p) {
     constexpr int N = 3 * M + 1;
     __shared__ dflt red[(kPSBlock / 32) * kPSBlock];
     __shared__ double blk[N];
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kPSBlock, pass_min_blocks<M>()) ps_kernel_f32(
 
 // FP64 accumulation (any storage): map, powers and sums in FP64.
 template <int M, int DT, bool MAP, int UNROLL>
-__global__ void __launch_bounds__(kPSBlock) ps_kernel_f64(PSParams p) {
+__global__ void __launch_bounds__(kPSBlock) ps_kernel_f64(__grid_constant__ const PSParams p) {
     constexpr int N = 3 * M + 1;
     __shared__ double red[(kPSBlock / 32) * kPSBlock];
     __shared__ double blk[N];

@@ -61,7 +61,7 @@ __device__ __forceinline__ void range_of_f32(const void* x, int64_t b, int64_t e
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kRgBlock) range_kernel(RgParams p) {
+__global__ void __launch_bounds__(kRgBlock) range_kernel(__grid_constant__ const RgParams p) {
     __shared__ int s_task;
     const int tid = threadIdx.x, lane = tid & 31;
     // one series range contributes through lane 0's atomics after a warp reduction

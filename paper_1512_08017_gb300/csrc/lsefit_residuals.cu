@@ -332,7 +332,7 @@ __device__ void rs_warp_task(const RsParams& p, int64_t s) {
 }
 
 template <int DT, bool CHEB>
-__global__ void __launch_bounds__(kRsBlock) residuals_kernel(RsParams p) {
+__global__ void __launch_bounds__(kRsBlock) residuals_kernel(__grid_constant__ const RsParams p) {
     __shared__ int s_task;
     __shared__ int s_last;
     __shared__ dflt red[(kRsBlock / 32) * kRsBlock];
