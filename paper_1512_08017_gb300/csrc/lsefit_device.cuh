@@ -150,22 +150,42 @@ struct Elem<LSEFIT_F64> {
     }
 };
 
-// 16-byte vector load that is not kept in L1 (streamed once).
+// L2 policy of data read once: its lines are the first to be replaced.  A
+// pass over more bytes than L2 holds would otherwise push out what the next
+// launch needs at once (its code, plan and per-series records), and a launch
+// of a few tens of microseconds then starts by waiting on DRAM for those.
+__device__ __forceinline__ unsigned long long l2_evict_first_policy() {
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// 16-byte vector load that is not kept in L1 and leaves L2 first (streamed once).
 __device__ __forceinline__ uint4 ld_stream16(const void* p) {
     uint4 r;
-    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
                  : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-                 : "l"(p));
+                 : "l"(p), "l"(l2_evict_first_policy()));
     return r;
+}
+
+// L2 prefetch of [p, p + bytes): a hint with nothing to wait for, holding no
+// registers (p 16-byte aligned, bytes a multiple of 16, the range inside one
+// allocation).
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // ---------------------------------------------------------------------------
 // Asynchronous global->shared copies (cp.async): in flight without holding
 // registers; cp.async.wait_group is a hardware wait on this thread's groups.
 // ---------------------------------------------------------------------------
+// (the streamed inputs: L2 evict-first, as ld_stream16)
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem_src) : "memory");
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem_src),
+                 "l"(l2_evict_first_policy())
+                 : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
