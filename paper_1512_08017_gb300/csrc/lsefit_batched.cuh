@@ -35,7 +35,10 @@
 
 namespace lsefit {
 
-constexpr int kBBlock = 512;
+#ifndef LSEFIT_BATCHED_BLOCK
+#define LSEFIT_BATCHED_BLOCK 512
+#endif
+constexpr int kBBlock = LSEFIT_BATCHED_BLOCK;  // threads of a persistent block (one per SM)
 constexpr int kBWarps = kBBlock / 32;
 constexpr int kDefaultWarpMaxLen = 65536;
 constexpr int kDefaultChunkLen = 65536;
@@ -165,10 +168,20 @@ __device__ __forceinline__ dflt bits_df(unsigned long long w) {
 // kStageBytes in the concatenated arrays, so every stage is a slice of one
 // aligned block and all but the first and last stage of a series are full.
 // ---------------------------------------------------------------------------
-constexpr int kRing = 3;                         // stages per warp ring
-constexpr int kStageBytes = 2048;                // bytes of x (and of y) per stage
+#ifndef LSEFIT_RING_STAGES
+#define LSEFIT_RING_STAGES 3
+#endif
+#ifndef LSEFIT_STAGE_BYTES
+#define LSEFIT_STAGE_BYTES 2048
+#endif
+#ifndef LSEFIT_FOLD_STAGES
+#define LSEFIT_FOLD_STAGES 2
+#endif
+constexpr int kRing = LSEFIT_RING_STAGES;        // stages per warp ring
+constexpr int kStageBytes = LSEFIT_STAGE_BYTES;  // bytes of x (and of y) per stage
 constexpr int kStageVecs = kStageBytes / 16;     // 16-byte vectors per stage (4 per lane)
-constexpr int kFoldStages = 2;                   // compensated batch = this many stages
+constexpr int kFoldStages = LSEFIT_FOLD_STAGES;  // compensated batch = this many stages
+static_assert(kRing >= 2 && kRing <= 3 && kStageVecs % 32 == 0, "ring geometry");
 #ifndef LSEFIT_STAGE_UNROLL
 #define LSEFIT_STAGE_UNROLL 1
 #endif
@@ -457,7 +470,7 @@ __device__ __forceinline__ bool issue_stage(const BParams& p, Ring& R, int slot,
 // Wait until the oldest of `pending` stages has landed, then make every
 // lane's copies visible to the warp.
 __device__ __forceinline__ void ring_wait(int pending) {
-    static_assert(kRing == 3, "ring_wait covers up to three pending stages");
+    static_assert(kRing <= 3, "ring_wait covers up to three pending stages");
     switch (pending) {
         case 1: cp_async_wait<0>(); break;
         case 2: cp_async_wait<1>(); break;

@@ -176,6 +176,11 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) 
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// L2 prefetch of the line that holds p (one thread's share of a coalesced prefetch).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // ---------------------------------------------------------------------------
 // Asynchronous global->shared copies (cp.async): in flight without holding
 // registers; cp.async.wait_group is a hardware wait on this thread's groups.

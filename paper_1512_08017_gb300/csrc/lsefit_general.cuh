@@ -229,8 +229,38 @@ __device__ __forceinline__ void split_range3(const void* x, const void* y, const
     }
 }
 
+// Grid steps the FP32 general pass prefetches into L2 ahead of its loads
+// (degrees up to 4, two blocks per SM): the prefetch of a block's slice of a later
+// step holds no registers, and the loads then find their lines in L2.
+#ifndef LSEFIT_GEN_PREFETCH_STEPS
+#define LSEFIT_GEN_PREFETCH_STEPS 8
+#endif
+constexpr int kGenPrefetchSteps = LSEFIT_GEN_PREFETCH_STEPS;
+
+// Degrees above 5 (one block per SM): groups of loads that each thread
+// prefetches into L2 ahead of the group it feeds, its own vectors.  The
+// unweighted pass also keeps its next group's loads in registers (the
+// pipeline); the weighted one has no registers for that.  Measured on the
+// degree-8 Chebyshev passes at 2^28 points: unweighted 0.54 of HBM with
+// neither, 0.58 with the pipeline alone, 0.62 with the pipeline and a
+// prefetch 8 groups ahead; weighted 0.68 without and 0.76 with a prefetch 4
+// groups ahead.
+#ifndef LSEFIT_GEN_PIPELINE
+#define LSEFIT_GEN_PIPELINE 1
+#endif
+#ifndef LSEFIT_GEN_THREAD_PREFETCH
+#define LSEFIT_GEN_THREAD_PREFETCH 8
+#endif
+constexpr int kGenThreadPrefetch = LSEFIT_GEN_THREAD_PREFETCH;     // with the pipeline
+#ifndef LSEFIT_GEN_THREAD_PREFETCH_W
+#define LSEFIT_GEN_THREAD_PREFETCH_W 4
+#endif
+constexpr int kGenThreadPrefetchW = LSEFIT_GEN_THREAD_PREFETCH_W;  // without it
+
 // FP32 arithmetic (FP32 or BF16 storage) over [b, e), map always applied
-// (identity constants when the caller gave no interval).
+// (identity constants when the caller gave no interval).  rank is
+// blockIdx.x * blockDim.x + threadIdx.x: a block's threads read consecutive
+// vectors at every grid step, the slice thread 0 prefetches.
 template <int M, int DT, bool COMP, bool W, bool CHEB, int UNROLL>
 __device__ __forceinline__ void accumulate_range_gen(AccGenF32<M, COMP, W, CHEB>& A, const void* x, const void* y,
                                                      const void* w, int64_t b, int64_t e, int64_t rank,
@@ -263,23 +293,98 @@ __device__ __forceinline__ void accumulate_range_gen(AccGenF32<M, COMP, W, CHEB>
             else A.template add_pair<false>(tp, yp, wp);
         }
     };
-    int64_t v = rank;
     constexpr int G = comp_groups<COMP, M, UNROLL, PV>();
-    for (; v + (G * UNROLL - 1) * nthreads < nvec; v += G * UNROLL * nthreads) {
+    constexpr int GU = G * UNROLL;
+    auto load_group = [&](uint4 (&xr)[UNROLL], uint4 (&yr)[UNROLL], uint4 (&wr)[UNROLL], int64_t o) {
 #pragma unroll
-        for (int gi = 0; gi < G; ++gi) {
-            uint4 xr[UNROLL], yr[UNROLL], wr[UNROLL];
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) {
-                const int64_t o = v + (gi * UNROLL + u) * nthreads;
-                xr[u] = ld_stream16(xv + o);
-                yr[u] = ld_stream16(yv + o);
-                wr[u] = W ? ld_stream16(wv + o) : make_uint4(0, 0, 0, 0);
-            }
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) feed(xr[u], yr[u], wr[u], gi == 0 && u == 0);
+        for (int u = 0; u < UNROLL; ++u) {
+            xr[u] = ld_stream16(xv + o + u * nthreads);
+            yr[u] = ld_stream16(yv + o + u * nthreads);
+            wr[u] = W ? ld_stream16(wv + o + u * nthreads) : make_uint4(0, 0, 0, 0);
         }
-        A.fold();
+    };
+    int64_t v = rank;
+    if constexpr (pass_min_blocks<M>() == 1 && !W && LSEFIT_GEN_PIPELINE) {
+        // One block per SM (unweighted, degrees above 5): each warp keeps the
+        // loads of its next group in flight while it feeds the current one,
+        // and prefetches the vectors of a later group into L2, so the loads of
+        // a scheduler's two warps are rarely all waiting on DRAM at once.
+        // (The weighted pass at these degrees has no registers for a second
+        // group: pipelined, it measured slower.)
+        if (v + (GU - 1) * nthreads < nvec) {
+            uint4 xr[UNROLL], yr[UNROLL], wr[UNROLL];
+            load_group(xr, yr, wr, v);
+            for (;;) {
+                const int64_t vn = v + GU * nthreads;
+                const bool more = vn + (GU - 1) * nthreads < nvec;
+#pragma unroll
+                for (int gi = 0; gi < G; ++gi) {
+                    if (kGenThreadPrefetch > 0) {
+                        const int64_t po = v + (gi + kGenThreadPrefetch) * UNROLL * nthreads;
+#pragma unroll
+                        for (int u = 0; u < UNROLL; ++u) {
+                            const int64_t q = min(po + u * nthreads, nvec - 1);
+                            prefetch_l2(xv + q);
+                            prefetch_l2(yv + q);
+                        }
+                    }
+                    uint4 xn[UNROLL], yn[UNROLL], wn[UNROLL];
+                    if (gi + 1 < G) load_group(xn, yn, wn, v + (gi + 1) * UNROLL * nthreads);
+                    else if (more) load_group(xn, yn, wn, vn);
+#pragma unroll
+                    for (int u = 0; u < UNROLL; ++u) feed(xr[u], yr[u], wr[u], gi == 0 && u == 0);
+#pragma unroll
+                    for (int u = 0; u < UNROLL; ++u) {
+                        xr[u] = xn[u];
+                        yr[u] = yn[u];
+                        wr[u] = wn[u];
+                    }
+                }
+                A.fold();
+                v = vn;
+                if (!more) break;
+            }
+        }
+    } else {
+        // Two blocks per SM: thread 0 prefetches the block's slice of the grid
+        // step kGenPrefetchSteps ahead into L2, so that the loads find it there
+        // (up to degree 4: degree 5 has no registers to spare for it).
+        const int64_t blk0 = rank - threadIdx.x;  // slice of step k: [blk0 + k nthreads, + blockDim.x)
+        auto prefetch_step = [&](int64_t k) {
+            const int64_t v0 = blk0 + k * nthreads;
+            if (v0 >= nvec) return;
+            const unsigned bytes = (unsigned)(min((int64_t)blockDim.x, nvec - v0) * 16);
+            prefetch_l2_bulk(xv + v0, bytes);
+            prefetch_l2_bulk(yv + v0, bytes);
+            if (W) prefetch_l2_bulk(wv + v0, bytes);
+        };
+        const bool prefetcher = kGenPrefetchSteps > 0 && M <= 4 && threadIdx.x == 0;
+        if (prefetcher)
+            for (int k = 0; k < kGenPrefetchSteps; ++k) prefetch_step(k);
+        int64_t step = 0;  // grid step of this iteration's first load
+        for (; v + (GU - 1) * nthreads < nvec; v += GU * nthreads, step += GU) {
+#pragma unroll
+            for (int gi = 0; gi < G; ++gi) {
+                uint4 xr[UNROLL], yr[UNROLL], wr[UNROLL];
+                if (pass_min_blocks<M>() == 1 && kGenThreadPrefetchW > 0) {
+                    const int64_t po = v + (gi + kGenThreadPrefetchW) * UNROLL * nthreads;
+#pragma unroll
+                    for (int u = 0; u < UNROLL; ++u) {
+                        const int64_t q = min(po + u * nthreads, nvec - 1);
+                        prefetch_l2(xv + q);
+                        prefetch_l2(yv + q);
+                        if (W) prefetch_l2(wv + q);
+                    }
+                }
+                if (prefetcher)
+#pragma unroll
+                    for (int u = 0; u < UNROLL; ++u) prefetch_step(step + gi * UNROLL + u + kGenPrefetchSteps);
+                load_group(xr, yr, wr, v + gi * UNROLL * nthreads);
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) feed(xr[u], yr[u], wr[u], gi == 0 && u == 0);
+            }
+            A.fold();
+        }
     }
     for (; v < nvec; v += nthreads) {
         feed(ld_stream16(xv + v), ld_stream16(yv + v), W ? ld_stream16(wv + v) : make_uint4(0, 0, 0, 0), true);
