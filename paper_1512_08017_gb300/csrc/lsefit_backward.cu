@@ -24,6 +24,12 @@
 namespace lsefit {
 
 constexpr int kBwBlock = 256;
+// Share of its points (1/kBwPrefetchDiv; 0: none) a gradient warp prefetches
+// into L2 while the lambda launch runs.
+#ifndef LSEFIT_BW_PREFETCH_DIV
+#define LSEFIT_BW_PREFETCH_DIV 2
+#endif
+constexpr int kBwPrefetchDiv = LSEFIT_BW_PREFETCH_DIV;
 
 struct BwParams {
     const void* x;
@@ -338,6 +344,32 @@ template <int DT>
 __global__ void __launch_bounds__(kBwBlock) grad_kernel(__grid_constant__ const BwParams p) {
     __shared__ int s_task;
     const int tid = threadIdx.x, lane = tid & 31;
+    // Tasks of one common length are split evenly by points over all warps
+    // (numbered warp-major, so every SM gets the same share): warp wid takes
+    // [wid * per, +per) of the points in reverse plan order.
+    const int64_t L = p.warp_task_len;
+    const int64_t total = (int64_t)p.n_warp_tasks * L;
+    const int64_t nw = (int64_t)gridDim.x * (kBwBlock / 32);
+    const int64_t wid = (int64_t)(tid >> 5) * gridDim.x + blockIdx.x;
+    const int64_t per = L > 0 ? ((total + nw - 1) / nw + 3) / 4 * 4 : 0;  // whole 16-byte vectors of FP32 points
+    if (kBwPrefetchDiv > 0 && L > 0 && p.n_block_tasks == 0) {
+        // While the lambda launch solves, DRAM is idle: bring the first part of
+        // this warp's points into L2 (the reads do not depend on lambda).
+        constexpr int ES = Elem<DT>::kSize, LINE = 128 / ES;  // points per 128-byte line
+        int64_t pos = min(total, wid * per);
+        const int64_t hi = min(total, pos + per / (kBwPrefetchDiv > 0 ? kBwPrefetchDiv : 1));
+        while (pos < hi) {
+            const int64_t r = pos / L;
+            const int64_t seg = min(hi, (r + 1) * L);
+            const int4 task = p.warp_tasks[p.n_warp_tasks - 1 - r];
+            const int64_t first = ((int64_t)(unsigned)task.z << 32) | (unsigned)task.y;
+            for (int64_t q = pos + (int64_t)lane * LINE; q < seg; q += 32 * LINE) {
+                prefetch_l2(static_cast<const char*>(p.x) + (first + (q - r * L)) * ES);
+                prefetch_l2(static_cast<const char*>(p.y) + (first + (q - r * L)) * ES);
+            }
+            pos = seg;
+        }
+    }
     // lambda, the FP32 copies and the queue counters come from the lambda launch
     griddep_wait();
     for (;;) {
@@ -355,16 +387,10 @@ __global__ void __launch_bounds__(kBwBlock) grad_kernel(__grid_constant__ const 
         grad_dispatch<DT>(p, s, b, e, tid, kBwBlock);
     }
     // warp tasks in reverse plan order: the forward pass read the last tasks of
-    // the plan last, so their points are the ones still held in L2.  Tasks of one
-    // common length are split evenly by points over all warps (numbered
-    // warp-major, so every SM gets the same share), which balances a batch of
-    // fewer tasks than twice the warps; otherwise warps draw whole tasks.
-    if (p.warp_task_len > 0) {
-        const int64_t L = p.warp_task_len;
-        const int64_t total = (int64_t)p.n_warp_tasks * L;
-        const int64_t nw = (int64_t)gridDim.x * (kBwBlock / 32);
-        const int64_t wid = (int64_t)(tid >> 5) * gridDim.x + blockIdx.x;
-        const int64_t per = ((total + nw - 1) / nw + 3) / 4 * 4;  // whole 16-byte vectors of FP32 points
+    // the plan last, so their points are the ones still held in L2.  The even
+    // split balances a batch of fewer tasks than twice the warps; tasks of
+    // different lengths are drawn whole.
+    if (L > 0) {
         int64_t pos = min(total, wid * per);
         const int64_t hi = min(total, pos + per);
         while (pos < hi) {
