@@ -92,6 +92,29 @@ def test_chebyshev_unscaled_interval(L, accum, m):
     _check(L, out, ref, accum, m)
 
 
+@pytest.mark.parametrize("offset", [0, 1])
+@pytest.mark.parametrize("weighted", [False, True])
+@pytest.mark.parametrize("m", [4, 8])
+def test_full_grid_iterations(L, m, weighted, offset):
+    """Enough points for several full iterations of the FP32 pass's main loop
+    at the largest grid, plus a ragged tail.  At degree 8 one iteration takes
+    152 blocks x 256 threads x 8 vectors (about 1.25M points), so smaller
+    cases run only the tail loop.  Degree 8 runs the register pipeline with the
+    per-thread L2 prefetch (unweighted) or the prefetch alone (weighted); degree 4
+    runs the block prefetch.  offset 1 starts x, y (and w) one element past a
+    16-byte boundary (three scalar head points)."""
+    n = 3 * 1_245_184 + 4097
+    d = synth.precision(n=n + offset, m=m, seed=97)
+    lo, hi = d["interval"]
+    x = _dev(d["x"])[offset:]
+    y = _dev(d["y"])[offset:]
+    wd = _dev(synth.weights(n + offset, seed=98))[offset:] if weighted else None
+    ref = oracle.fit_general_interval(_stored(x), _stored(y), m, lo, hi, fp32=True,
+                                      w=_stored(wd) if weighted else None, basis="chebyshev")
+    out = L.fit_general(x, y, m, w=wd, basis="chebyshev", accum="comp", interval=(lo, hi))
+    _check(L, out, ref, "comp", m, n=n)
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float64])
 @pytest.mark.parametrize("m", [2, 5, 6, 8])
 def test_weighted_chebyshev_storage(L, dtype, m):
