@@ -115,6 +115,20 @@ def test_full_grid_iterations(L, m, weighted, offset):
     _check(L, out, ref, "comp", m, n=n)
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("m", [6, 7, 8])
+def test_unweighted_monomial_high_degree(L, m, dtype):
+    """The unweighted pass above degree 5 in the monomial basis (its slots are
+    split over warp pairs), compensated and naive, against the oracle."""
+    n = 2 * 1_245_184 + 777
+    d = synth.small_series(n, seed=99 + m, lo=-2.0, hi=6.0, m=m, dtype=np.float64)
+    x, y = _dev(d["x"], dtype), _dev(d["y"], dtype)
+    for accum in ("comp", "naive"):
+        ref = oracle.fit_general_interval(_stored(x), _stored(y), m, -2.0, 6.0, fp32=True)
+        out = L.fit_general(x, y, m, accum=accum, interval=(-2.0, 6.0))
+        _check(L, out, ref, accum, m, n=n)
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float64])
 @pytest.mark.parametrize("m", [2, 5, 6, 8])
 def test_weighted_chebyshev_storage(L, dtype, m):
