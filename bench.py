@@ -55,6 +55,8 @@ def parse_args(argv=None):
     p.add_argument("--no-plain", action="store_true", help="skip the plain per-series comparison")
     p.add_argument("--coef-sample", type=int, default=2048,
                    help="series of a batch checked against the oracle after the timed region")
+    p.add_argument("--no-coef", action="store_true",
+                   help="general workload: skip the oracle check of the timed coefficients")
     p.add_argument("--no-sub", action="store_true",
                    help="default workload: skip the ragged and differentiable sub-records")
     p.add_argument("--tuning", default=None,
@@ -297,6 +299,33 @@ def rel_err(a, b) -> float:
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def coef_err_general(out, ref, m: int, accum: str, n: int, status: str) -> dict:
+    """Error of the timed general fit of degree m (row m - 1 of the outputs, m_lo =
+    1; status: its name) against the oracle's fit of the same stored points: relative errors of the
+    basis and monomial coefficients, the normwise backward error of Xb in the
+    oracle's G Xb = b, cond(G), and the gates the parity tests apply (forward:
+    max(base, cond eps 4m) while at most 1e-3; backward: 1e-5 compensated, 1e-12 +
+    2n 2^-53 FP64)."""
+    rec = {"degree": m, "status": status, "oracle_status": ref["status"]}
+    if rec["status"] != "ok" or ref["status"] != "ok":
+        return rec
+    Xb = np.asarray(out["Xb"][m - 1][: m + 1], dtype=np.float64)
+    X = np.asarray(out["X"][m - 1][: m + 1], dtype=np.float64)
+    G = np.asarray(ref["G"], dtype=np.float64)
+    b = np.asarray(ref["b"], dtype=np.float64)
+    cond = float(np.linalg.cond(G))
+    eps, base = (2.0 ** -53, 1e-6) if accum == "f64" else (2.0 ** -24, 1e-5)
+    fwd_gate = max(base, cond * eps * 4 * m)
+    rec.update({
+        "rel_Xb": rel_err(Xb, ref["Xb"]), "rel_X": rel_err(X, ref["X"]),
+        "backward": float(np.linalg.norm(G @ Xb - b) / (np.linalg.norm(G, 2) * np.linalg.norm(Xb) + np.linalg.norm(b))),
+        "cond_G": cond,
+        "forward_gate": fwd_gate if fwd_gate <= 1e-3 else None,
+        "backward_gate": 1e-12 + 2.0 * n * 2.0 ** -53 if accum == "f64" else (1e-3 if accum == "naive" else 1e-5),
+    })
+    return rec
 
 
 def backward_err(S, T, m, Xt) -> float:
@@ -1188,6 +1217,8 @@ def run_general(args, dist: Dist):
     per, total = _event_steps(step, args.steps, stream)
     dist.barrier()
     clk = clocks.stop()
+    timed = {k: out[k].cpu().numpy() for k in ("X", "Xb")}
+    timed_status = L.status_names(out["status"])[m - 1]
     ms_max = dist.max(total)
     kern_ms = dist.max(statistics.mean(per))
     streams = 3 if weighted else 2
@@ -1232,6 +1263,16 @@ def run_general(args, dist: Dist):
                "mode": "mapped" if best is mapped_mode else "copy", "copy": copy_mode, "mapped": mapped_mode}
     kname = "gen_kernel_{}<{},F32,{},W={},CHEB={}>".format("f64" if accum == "f64" else "f32", m, accum,
                                                           int(weighted), int(basis == "chebyshev"))
+    coef = None
+    if dist.rank == 0 and not args.no_coef:
+        # the timed coefficients of degree m against the oracle on all n stored points
+        import oracle
+        t0 = time.perf_counter()
+        ref = oracle.fit_general_interval(hx.numpy(), hy.numpy(), m, lo, hi, fp32=accum != "f64",
+                                          w=hw.numpy() if weighted else None, basis=basis)
+        coef = coef_err_general(timed, ref, m, accum, n, timed_status)
+        coef.update({"oracle": f"sequential FP64 oracle (fit_general) on all {n} stored points; degrees "
+                               f"{m - 1}..1 come from the same pass", "oracle_s": time.perf_counter() - t0})
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_general(d["x"] if (lo, hi) == (-1.0, 1.0) else hx.numpy(), d["y"],
@@ -1247,7 +1288,7 @@ def run_general(args, dist: Dist):
                    "parallelism": f"replicas x{dist.world}"},
         "roofline": _roofline(algo_bytes, kern_ms, kname, f"general_{args.kind}") if accum != "f64" else
         _roofline_fp64(n * (8 * m + 2 + (3 if weighted else 0)), kern_ms, kname),
-        "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": args.steps,
+        "coef_err": coef, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": args.steps,
     }
 
 

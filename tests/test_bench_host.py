@@ -112,3 +112,25 @@ def test_host_placement_helpers():
     assert isinstance(nodes, dict)
     for k, v in nodes.items():
         assert k >= 0 and isinstance(v, str)
+
+
+def test_general_coefficient_record():
+    """coef_err_general: zero error for the oracle's own solution, a planted
+    error shows in both coefficient sets and in the backward error, and a status
+    other than ok reports no error figures."""
+    import numpy as np
+    import oracle
+    import synth
+    d = synth.small_series(5000, seed=3, lo=-1.0, hi=1.0, m=4, dtype=np.float64)
+    ref = oracle.fit_general_interval(d["x"].astype(np.float32), d["y"].astype(np.float32), 4, -1.0, 1.0,
+                                      fp32=True, basis="chebyshev")
+    out = {"Xb": np.tile(np.append(ref["Xb"], 0.0), (4, 1)), "X": np.tile(np.append(ref["X"], 0.0), (4, 1))}
+    rec = bench.coef_err_general(out, ref, 4, "comp", 5000, "ok")
+    assert rec["rel_Xb"] == 0.0 and rec["rel_X"] == 0.0 and rec["backward"] < 1e-15
+    assert rec["forward_gate"] == 1e-5 and rec["backward_gate"] == 1e-5
+    out["Xb"][3, 2] *= 1.1
+    out["X"][3, 2] *= 1.1
+    bad = bench.coef_err_general(out, ref, 4, "comp", 5000, "ok")
+    assert bad["rel_Xb"] > 1e-5 and bad["rel_X"] > 1e-5 and bad["backward"] > 1e-6
+    assert bench.coef_err_general(out, ref, 4, "f64", 5000, "singular") == {
+        "degree": 4, "status": "singular", "oracle_status": "ok"}
