@@ -338,22 +338,25 @@ def backward_err(S, T, m, Xt) -> float:
     return float(np.linalg.norm(A @ Xt - B) / (np.linalg.norm(A, 2) * np.linalg.norm(Xt) + np.linalg.norm(B)))
 
 
-def coef_err_single(x: np.ndarray, y: np.ndarray, out: dict, m: int, m_lo: int = 1) -> dict:
+def coef_err_single(x: np.ndarray, y: np.ndarray, out: dict, m: int, m_lo: int = 1, accum: str = "comp") -> dict:
     """Error of the timed single-series result (every degree m_lo..m, no interval)
-    against the sequential FP64 oracle on all the stored points."""
+    against the sequential FP64 oracle on all the stored points (singular
+    threshold of the accumulation)."""
     import oracle
+    eps = oracle.EPS64 if accum == "f64" else oracle.EPS32
     t0 = time.perf_counter()
-    ref = oracle.fit(x.astype(np.float64), y.astype(np.float64), m, eps=oracle.EPS32)
+    ref = oracle.fit(x.astype(np.float64), y.astype(np.float64), m, eps=eps)
     X = out["X"].cpu().numpy()
     Xt = out["Xt"].cpu().numpy()
     per = []
     for r, d in enumerate(range(m_lo, m + 1)):
-        st, Xo = oracle.solve(ref["S"][: 2 * d + 1], ref["T"][: d + 1], d, eps=oracle.EPS32)
+        st, Xo = oracle.solve(ref["S"][: 2 * d + 1], ref["T"][: d + 1], d, eps=eps)
         per.append({"m": d, "status": st, "X": rel_err(X[r, : d + 1], Xo), "Xt": rel_err(Xt[r, : d + 1], Xo),
                     "backward": backward_err(ref["S"], ref["T"], d, Xt[r, : d + 1])})
     return {"max_rel_X": max(p["X"] for p in per), "max_rel_Xt": max(p["Xt"] for p in per),
             "max_backward": max(p["backward"] for p in per), "per_degree": per,
-            "tolerance": 1e-5, "oracle": f"sequential FP64 oracle on all {x.size} stored points",
+            "tolerance": 1e-6 if accum == "f64" else 1e-5,
+            "oracle": f"sequential FP64 oracle on all {x.size} stored points",
             "oracle_s": time.perf_counter() - t0}
 
 
@@ -1078,6 +1081,26 @@ def run_solve(args, dist: Dist):
     both = ok & (res["gauss"]["status"] == 0) & (res["cholesky"]["status"] == 0)
     a, c = res["gauss"]["Xt"][both], res["cholesky"]["Xt"][both]
     agree = float(((a - c).norm(dim=1) / a.norm(dim=1)).max().item())
+    # the GPU elimination against the oracle's on the same FP64 sums, every system
+    import oracle
+    t0 = time.perf_counter()
+    sh = sums.cpu().numpy()
+    Xg = res["gauss"]["Xt"].cpu().numpy()
+    stg = res["gauss"]["status"].cpu().numpy()
+    okh = ok.cpu().numpy()
+    worst = bmax = 0.0
+    mism = 0
+    for i in np.nonzero(okh)[0]:
+        st_o, Xo = oracle.solve(sh[i, : 2 * m + 1], sh[i, 2 * m + 1: 3 * m + 2], m, eps=oracle.EPS32)
+        if (st_o == "ok") != (stg[i] == 0):
+            mism += 1
+            continue
+        if st_o == "ok":
+            worst = max(worst, rel_err(Xg[i], Xo))
+            bmax = max(bmax, backward_err(sh[i, : 2 * m + 1], sh[i, 2 * m + 1:], m, Xg[i]))
+    coef = {"systems_checked": int(okh.sum()), "status_mismatches": mism, "max_rel_Xt": worst,
+            "max_backward": bmax, "oracle": "the oracle's Gaussian elimination on the same FP64 sums",
+            "oracle_s": time.perf_counter() - t0}
     n1 = m + 1
     flops = {"gauss": 2 * n1 ** 3 / 3 + 2 * n1 ** 2, "cholesky": n1 ** 3 / 3 + 2 * n1 ** 2}
     out = {}
@@ -1093,7 +1116,8 @@ def run_solve(args, dist: Dist):
             "data": "synthetic (power sums of the seeded ragged batch fitted at degree 5)",
             "config": {"workload": f"{S} degree-5 normal-equation systems from one batched pass, "
                                    "one system per thread", "series": S, "m": m},
-            "gauss": out["gauss"], "cholesky": out["cholesky"], "max_rel_diff_gauss_cholesky": agree, "clocks": clk,
+            "gauss": out["gauss"], "cholesky": out["cholesky"], "max_rel_diff_gauss_cholesky": agree,
+            "coef_err": coef, "clocks": clk,
             "roofline": {"bound": "fp64 latency", "achieved": out["gauss"]["gflops"], "peak": 1250.0,
                          "unit": "GFLOP/s", "frac": out["gauss"]["gflops"] / 1250.0, "traffic": None,
                          "peak_source": "nominal FP64 (no measured FP64 figure)"},
@@ -1127,7 +1151,9 @@ def run_single_fp64(args, dist: Dist):
     dist.barrier()
     clk = clocks.stop()
     ms = dist.max(total) / args.steps
+    coef = coef_err_single(d["x"], d["y"], out, 3, 1, accum="f64") if dist.rank == 0 else None
     return {"metric": "fit latency (FP64, degrees 1-3 in one launch)", "clocks": clk, "value": ms * 1e3, "unit": "us",
+            "coef_err": coef,
             "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded)", "points_per_s": n / (ms / 1e3),
