@@ -12,6 +12,14 @@
 
 namespace lsefit {
 
+// Threads per block of the preparation launch: one warp, because the map
+// constants cost FP64 divisions, which a scheduler issues a few per hundred
+// cycles, so they are spread over as many SMs as the series allow.
+#ifndef LSEFIT_PREP_THREADS
+#define LSEFIT_PREP_THREADS 32
+#endif
+constexpr int kPrepThreads = LSEFIT_PREP_THREADS;
+
 static batched_kernel_t pick_batched(int dtype, int accum, int nmax, int basis) {
     if (basis == LSEFIT_BASIS_CHEBYSHEV) {
         if (dtype == LSEFIT_F64) return batched_f64_f64_cheb(nmax);
@@ -276,7 +284,7 @@ extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* 
         for (int k = c + 1; k <= kClasses; ++k) p.cls_block[k] = (int)grid;
     }
     {
-        const int pt = 256;
+        const int pt = kPrepThreads;
         const int64_t items = std::max<int64_t>(std::max<int64_t>(b.num_series, plan->n_block_tasks), kCounters);
         const int64_t pb = (items + pt - 1) / pt;
         auto prep = b.accum == LSEFIT_ACCUM_F64 ? batched_prep_kernel<false> : batched_prep_kernel<true>;
