@@ -2,10 +2,31 @@
 // (per-point weights, Chebyshev basis): argument checks, launch shape and
 // the C entry points.  The kernels are in lsefit_general.cuh, instantiated
 // one kind per translation unit (lsefit_general_{w,c,wc}.cu).
+#include <mutex>
+#include <unordered_map>
+
 #include "lsefit_general.cuh"
 #include "lsefit_host.h"
 
 using namespace lsefit;
+
+// Threads per block a general kernel was compiled for (its __launch_bounds__),
+// per device and kernel.
+static int block_threads_of(const void* kernel) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> cache[256];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return kGenBlock;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache[dev].find(kernel);
+    if (it != cache[dev].end()) return it->second;
+    cudaFuncAttributes a;
+    int t = kGenBlock;
+    if (cudaFuncGetAttributes(&a, kernel) == cudaSuccess && a.maxThreadsPerBlock >= 32) t = a.maxThreadsPerBlock;
+    else (void)cudaGetLastError();
+    cache[dev][kernel] = t;
+    return t;
+}
 
 extern "C" size_t lsefit_fit_general_workspace_size(int m) {
     if (m < 1 || m > LSEFIT_MAX_DEGREE_CHEBYSHEV) return 0;
@@ -62,13 +83,14 @@ extern "C" int lsefit_fit_general(const void* x, const void* y, const void* w, i
     int dev = 0;
     const int sms = current_sm_count(&dev);
     if (sms <= 0) return LSEFIT_ERR_CUDA;
-    const int occ = occupancy_blocks(reinterpret_cast<const void*>(k), kGenBlock, 0);
+    const int threads = block_threads_of(reinterpret_cast<const void*>(k));
+    const int occ = occupancy_blocks(reinterpret_cast<const void*>(k), threads, 0);
     const int64_t work = (n + 16 / elem_size(dtype) - 1) / (16 / elem_size(dtype));
     int64_t grid = (int64_t)sms * occ;
-    const int64_t want = (work + 2 * kGenBlock - 1) / (2 * kGenBlock);
+    const int64_t want = (work + 2 * threads - 1) / (2 * threads);
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
     if (grid > kMaxGrid) grid = kMaxGrid;
-    k<<<(unsigned)grid, kGenBlock, 0, (cudaStream_t)stream>>>(p);
+    k<<<(unsigned)grid, threads, 0, (cudaStream_t)stream>>>(p);
     return cudaGetLastError() == cudaSuccess ? LSEFIT_OK : LSEFIT_ERR_CUDA;
 }

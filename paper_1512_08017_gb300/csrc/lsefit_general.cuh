@@ -237,25 +237,15 @@ __device__ __forceinline__ void split_range3(const void* x, const void* y, const
 #endif
 constexpr int kGenPrefetchSteps = LSEFIT_GEN_PREFETCH_STEPS;
 
-// Degrees above 5 (one block per SM): groups of loads that each thread
-// prefetches into L2 ahead of the group it feeds, its own vectors.  The
-// unweighted pass also keeps its next group's loads in registers (the
-// pipeline); the weighted one has no registers for that.  Measured on the
-// degree-8 Chebyshev passes at 2^28 points: unweighted 0.54 of HBM with
-// neither, 0.58 with the pipeline alone, 0.62 with the pipeline and a
-// prefetch 8 groups ahead; weighted 0.68 without and 0.76 with a prefetch 4
-// groups ahead.
-#ifndef LSEFIT_GEN_PIPELINE
-#define LSEFIT_GEN_PIPELINE 1
-#endif
+// Degrees above 5 (one block per SM): groups of loads ahead of the group
+// being fed that each thread prefetches into L2, its own vectors.  Measured
+// on the degree-8 Chebyshev passes at 2^28 points: weighted 0.68 of HBM
+// without and 0.76 with a prefetch 4 groups ahead; unweighted 0.54 without,
+// 0.65-0.66 with it at 384 threads per block (below).
 #ifndef LSEFIT_GEN_THREAD_PREFETCH
-#define LSEFIT_GEN_THREAD_PREFETCH 8
+#define LSEFIT_GEN_THREAD_PREFETCH 4
 #endif
-constexpr int kGenThreadPrefetch = LSEFIT_GEN_THREAD_PREFETCH;     // with the pipeline
-#ifndef LSEFIT_GEN_THREAD_PREFETCH_W
-#define LSEFIT_GEN_THREAD_PREFETCH_W 4
-#endif
-constexpr int kGenThreadPrefetchW = LSEFIT_GEN_THREAD_PREFETCH_W;  // without it
+constexpr int kGenThreadPrefetch = LSEFIT_GEN_THREAD_PREFETCH;
 
 // FP32 arithmetic (FP32 or BF16 storage) over [b, e), map always applied
 // (identity constants when the caller gave no interval).  rank is
@@ -304,87 +294,46 @@ __device__ __forceinline__ void accumulate_range_gen(AccGenF32<M, COMP, W, CHEB>
         }
     };
     int64_t v = rank;
-    if constexpr (pass_min_blocks<M>() == 1 && !W && LSEFIT_GEN_PIPELINE) {
-        // One block per SM (unweighted, degrees above 5): each warp keeps the
-        // loads of its next group in flight while it feeds the current one,
-        // and prefetches the vectors of a later group into L2, so the loads of
-        // a scheduler's two warps are rarely all waiting on DRAM at once.
-        // (The weighted pass at these degrees has no registers for a second
-        // group: pipelined, it measured slower.)
-        if (v + (GU - 1) * nthreads < nvec) {
+    // L2 prefetch ahead of the loads.  Up to degree 4 (two blocks per SM)
+    // thread 0 prefetches the block's slice of the grid step kGenPrefetchSteps
+    // ahead (degree 5 has no registers to spare for it); above degree 5 (one
+    // block per SM) each thread prefetches its own vectors kGenThreadPrefetch
+    // groups ahead.
+    const int64_t blk0 = rank - threadIdx.x;  // slice of step k: [blk0 + k nthreads, + blockDim.x)
+    auto prefetch_step = [&](int64_t k) {
+        const int64_t v0 = blk0 + k * nthreads;
+        if (v0 >= nvec) return;
+        const unsigned bytes = (unsigned)(min((int64_t)blockDim.x, nvec - v0) * 16);
+        prefetch_l2_bulk(xv + v0, bytes);
+        prefetch_l2_bulk(yv + v0, bytes);
+        if (W) prefetch_l2_bulk(wv + v0, bytes);
+    };
+    const bool prefetcher = kGenPrefetchSteps > 0 && M <= 4 && threadIdx.x == 0;
+    if (prefetcher)
+        for (int k = 0; k < kGenPrefetchSteps; ++k) prefetch_step(k);
+    int64_t step = 0;  // grid step of this iteration's first load
+    for (; v + (GU - 1) * nthreads < nvec; v += GU * nthreads, step += GU) {
+#pragma unroll
+        for (int gi = 0; gi < G; ++gi) {
             uint4 xr[UNROLL], yr[UNROLL], wr[UNROLL];
-            load_group(xr, yr, wr, v);
-            for (;;) {
-                const int64_t vn = v + GU * nthreads;
-                const bool more = vn + (GU - 1) * nthreads < nvec;
+            if (pass_min_blocks<M>() == 1 && kGenThreadPrefetch > 0) {
+                const int64_t po = v + (gi + kGenThreadPrefetch) * UNROLL * nthreads;
 #pragma unroll
-                for (int gi = 0; gi < G; ++gi) {
-                    if (kGenThreadPrefetch > 0) {
-                        const int64_t po = v + (gi + kGenThreadPrefetch) * UNROLL * nthreads;
-#pragma unroll
-                        for (int u = 0; u < UNROLL; ++u) {
-                            const int64_t q = min(po + u * nthreads, nvec - 1);
-                            prefetch_l2(xv + q);
-                            prefetch_l2(yv + q);
-                        }
-                    }
-                    uint4 xn[UNROLL], yn[UNROLL], wn[UNROLL];
-                    if (gi + 1 < G) load_group(xn, yn, wn, v + (gi + 1) * UNROLL * nthreads);
-                    else if (more) load_group(xn, yn, wn, vn);
-#pragma unroll
-                    for (int u = 0; u < UNROLL; ++u) feed(xr[u], yr[u], wr[u], gi == 0 && u == 0);
-#pragma unroll
-                    for (int u = 0; u < UNROLL; ++u) {
-                        xr[u] = xn[u];
-                        yr[u] = yn[u];
-                        wr[u] = wn[u];
-                    }
+                for (int u = 0; u < UNROLL; ++u) {
+                    const int64_t q = min(po + u * nthreads, nvec - 1);
+                    prefetch_l2(xv + q);
+                    prefetch_l2(yv + q);
+                    if (W) prefetch_l2(wv + q);
                 }
-                A.fold();
-                v = vn;
-                if (!more) break;
             }
+            if (prefetcher)
+#pragma unroll
+                for (int u = 0; u < UNROLL; ++u) prefetch_step(step + gi * UNROLL + u + kGenPrefetchSteps);
+            load_group(xr, yr, wr, v + gi * UNROLL * nthreads);
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) feed(xr[u], yr[u], wr[u], gi == 0 && u == 0);
         }
-    } else {
-        // Two blocks per SM: thread 0 prefetches the block's slice of the grid
-        // step kGenPrefetchSteps ahead into L2, so that the loads find it there
-        // (up to degree 4: degree 5 has no registers to spare for it).
-        const int64_t blk0 = rank - threadIdx.x;  // slice of step k: [blk0 + k nthreads, + blockDim.x)
-        auto prefetch_step = [&](int64_t k) {
-            const int64_t v0 = blk0 + k * nthreads;
-            if (v0 >= nvec) return;
-            const unsigned bytes = (unsigned)(min((int64_t)blockDim.x, nvec - v0) * 16);
-            prefetch_l2_bulk(xv + v0, bytes);
-            prefetch_l2_bulk(yv + v0, bytes);
-            if (W) prefetch_l2_bulk(wv + v0, bytes);
-        };
-        const bool prefetcher = kGenPrefetchSteps > 0 && M <= 4 && threadIdx.x == 0;
-        if (prefetcher)
-            for (int k = 0; k < kGenPrefetchSteps; ++k) prefetch_step(k);
-        int64_t step = 0;  // grid step of this iteration's first load
-        for (; v + (GU - 1) * nthreads < nvec; v += GU * nthreads, step += GU) {
-#pragma unroll
-            for (int gi = 0; gi < G; ++gi) {
-                uint4 xr[UNROLL], yr[UNROLL], wr[UNROLL];
-                if (pass_min_blocks<M>() == 1 && kGenThreadPrefetchW > 0) {
-                    const int64_t po = v + (gi + kGenThreadPrefetchW) * UNROLL * nthreads;
-#pragma unroll
-                    for (int u = 0; u < UNROLL; ++u) {
-                        const int64_t q = min(po + u * nthreads, nvec - 1);
-                        prefetch_l2(xv + q);
-                        prefetch_l2(yv + q);
-                        if (W) prefetch_l2(wv + q);
-                    }
-                }
-                if (prefetcher)
-#pragma unroll
-                    for (int u = 0; u < UNROLL; ++u) prefetch_step(step + gi * UNROLL + u + kGenPrefetchSteps);
-                load_group(xr, yr, wr, v + gi * UNROLL * nthreads);
-#pragma unroll
-                for (int u = 0; u < UNROLL; ++u) feed(xr[u], yr[u], wr[u], gi == 0 && u == 0);
-            }
-            A.fold();
-        }
+        A.fold();
     }
     for (; v < nvec; v += nthreads) {
         feed(ld_stream16(xv + v), ld_stream16(yv + v), W ? ld_stream16(wv + v) : make_uint4(0, 0, 0, 0), true);
@@ -448,6 +397,13 @@ __device__ __forceinline__ void accumulate_range_gen_f64(AccGenF64<M, W, CHEB>& 
 // the last block combines them in a fixed order and solves).
 // ---------------------------------------------------------------------------
 constexpr int kGenBlock = 256;
+// Threads per block of the unweighted pass above degree 5 (one block per SM):
+// 384 fits its 26 slots in 166 registers, 12 warps per SM where 256 threads
+// gave 8.  Chebyshev m = 8 at 2^28 points: 0.65-0.66 of HBM against 0.61
+// (320 threads, whose 10 warps split unevenly over the 4 schedulers: 0.57).
+#ifndef LSEFIT_GEN_HI_BLOCK
+#define LSEFIT_GEN_HI_BLOCK 384
+#endif
 
 struct GenParams {
     const void* x;
@@ -522,19 +478,19 @@ __device__ void gen_publish(const GenParams& p, const double* blk, bool map_ok, 
     if (tid < 32 && tid <= M - p.m_lo) gen_solve_degree<M, W, CHEB>(p, tot_s, c, s, map_ok, tid);
 }
 
-template <int M, int DT, bool COMP, bool W, bool CHEB, int UNROLL>
-__global__ void __launch_bounds__(kGenBlock, pass_min_blocks<M>()) gen_kernel_f32(__grid_constant__ const GenParams p) {
+template <int M, int DT, bool COMP, bool W, bool CHEB, int UNROLL, int BLOCK = kGenBlock>
+__global__ void __launch_bounds__(BLOCK, pass_min_blocks<M>()) gen_kernel_f32(__grid_constant__ const GenParams p) {
     constexpr int N = 3 * M + 2;
-    __shared__ dflt red[(kGenBlock / 32) * kGenBlock];
+    __shared__ dflt red[(BLOCK / 32) * BLOCK];
     __shared__ double blk[N];
     double cd, sd;
     const bool map_ok = map_constants(p.interval, true, cd, sd);
     AccGenF32<M, COMP, W, CHEB> A;
     A.init();
-    const int64_t nthr = (int64_t)gridDim.x * kGenBlock;
-    const int64_t gtid = (int64_t)blockIdx.x * kGenBlock + threadIdx.x;
+    const int64_t nthr = (int64_t)gridDim.x * BLOCK;
+    const int64_t gtid = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
     accumulate_range_gen<M, DT, COMP, W, CHEB, UNROLL>(A, p.x, p.y, p.w, 0, p.n, gtid, nthr, (float)cd, (float)sd);
-    block_reduce_df<kGenBlock, N>([&](int a) { return A.result(a); }, red, blk);
+    block_reduce_df<BLOCK, N>([&](int a) { return A.result(a); }, red, blk);
     gen_publish<M, W, CHEB>(p, blk, map_ok, cd, sd);
 }
 
@@ -567,9 +523,10 @@ gen_kernel_t gen_pick_m(int dtype, int accum) {
     }
     if (dtype == LSEFIT_F64) return nullptr;
     const bool comp = accum == LSEFIT_ACCUM_COMP;
+    constexpr int B = (!W && pass_min_blocks<M>() == 1) ? LSEFIT_GEN_HI_BLOCK : kGenBlock;
     if (dtype == LSEFIT_F32)
-        return comp ? gen_kernel_f32<M, LSEFIT_F32, true, W, CHEB, U> : gen_kernel_f32<M, LSEFIT_F32, false, W, CHEB, U>;
-    return comp ? gen_kernel_f32<M, LSEFIT_BF16, true, W, CHEB, 2> : gen_kernel_f32<M, LSEFIT_BF16, false, W, CHEB, 2>;
+        return comp ? gen_kernel_f32<M, LSEFIT_F32, true, W, CHEB, U, B> : gen_kernel_f32<M, LSEFIT_F32, false, W, CHEB, U, B>;
+    return comp ? gen_kernel_f32<M, LSEFIT_BF16, true, W, CHEB, 2, B> : gen_kernel_f32<M, LSEFIT_BF16, false, W, CHEB, 2, B>;
 }
 
 template <bool W, bool CHEB>
