@@ -397,9 +397,10 @@ __device__ __forceinline__ void accumulate_range_gen_f64(AccGenF64<M, W, CHEB>& 
 // the last block combines them in a fixed order and solves).
 // ---------------------------------------------------------------------------
 constexpr int kGenBlock = 256;
-// Threads per block of the unweighted pass above degree 5 (one block per SM):
-// 384 fits its 26 slots in 166 registers, 12 warps per SM where 256 threads
-// gave 8.  Chebyshev m = 8 at 2^28 points: 0.65-0.66 of HBM against 0.61
+// Threads per block of the pass above degree 5 (one block per SM): at 384 the
+// compiler fits the 26 slots of degree 8 in 166-168 registers, 12 warps per
+// SM where 256 threads gave 8.  At 2^28 points, Chebyshev m = 8 runs at
+// 0.67-0.68 of HBM against 0.61, weighted Chebyshev at 0.78 against 0.75
 // (320 threads, whose 10 warps split unevenly over the 4 schedulers: 0.57).
 #ifndef LSEFIT_GEN_HI_BLOCK
 #define LSEFIT_GEN_HI_BLOCK 384
@@ -523,7 +524,7 @@ gen_kernel_t gen_pick_m(int dtype, int accum) {
     }
     if (dtype == LSEFIT_F64) return nullptr;
     const bool comp = accum == LSEFIT_ACCUM_COMP;
-    constexpr int B = (!W && pass_min_blocks<M>() == 1) ? LSEFIT_GEN_HI_BLOCK : kGenBlock;
+    constexpr int B = pass_min_blocks<M>() == 1 ? LSEFIT_GEN_HI_BLOCK : kGenBlock;
     if (dtype == LSEFIT_F32)
         return comp ? gen_kernel_f32<M, LSEFIT_F32, true, W, CHEB, U, B> : gen_kernel_f32<M, LSEFIT_F32, false, W, CHEB, U, B>;
     return comp ? gen_kernel_f32<M, LSEFIT_BF16, true, W, CHEB, 2, B> : gen_kernel_f32<M, LSEFIT_BF16, false, W, CHEB, 2, B>;
