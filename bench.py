@@ -875,7 +875,7 @@ def run_diff_batch(args, dist: Dist):
         tuning = json.loads(args.tuning)
     else:
         tuning, _ = autotune.tune_batched(x, y, off, deg, iv, m_max=m, accum=args.accum)
-    plan = L.BatchPlan(offsets, m, tuning=tuning, device=dev)
+    plan = L.BatchPlan(offsets, m, tuning=tuning, device=dev, degree=deg)
     fwd_out = {"X": torch.empty(S, m + 1, dtype=torch.float64, device=dev),
                "Xt": torch.empty(S, m + 1, dtype=torch.float64, device=dev),
                "sums": torch.empty(S, 3 * m + 2, dtype=torch.float64, device=dev),

@@ -436,8 +436,12 @@ int lsefit_plan_autotune_sizes(const int64_t* offsets_host, const int32_t* degre
  * same Section II fit under every schedule; only the assignment of series to
  * warps and blocks changes).  For each candidate: the plan is built on the
  * host for the layout (offsets_host, degree_host), its task arrays copied
- * into tasks_device, one warm-up fit, then `reps` fits timed with CUDA events
- * on `stream`.  Synchronous: returns after the last measurement.  Outputs of
+ * into tasks_device, one warm-up fit on `stream`, then the fit captured in a
+ * CUDA graph (on a private stream) and `reps` replays of it timed with CUDA
+ * events on `stream` -- the way a caller that replays graphs runs the fit;
+ * timed as plain back-to-back calls, schedules can differ by less than the
+ * noise while their graph replays do not.  Synchronous: returns after the
+ * last measurement.  Outputs of
  * the trial fits land in X and status (their content is the last
  * candidate's fit).  Build the final plan with lsefit_plan_build(*best).
  *  batch          host descriptor of the device batch (as lsefit_fit_batched).
@@ -452,7 +456,8 @@ int lsefit_plan_autotune_sizes(const int64_t* offsets_host, const int32_t* degre
  *  X, status      device outputs as for lsefit_fit_batched.
  *  best           host, written: the resolved tuning of the fastest candidate.
  *  ms_per_candidate  host float[n_candidates] or NULL: mean ms per fit.
- * Allocates no device memory (two CUDA events are created and destroyed).
+ * Allocates no device memory of its own: two CUDA events, a stream and one
+ * graph per candidate are created and destroyed.
  */
 int lsefit_plan_autotune(const lsefit_batch* batch, const int64_t* offsets_host, const int32_t* degree_host,
                          const lsefit_tuning* candidates, int n_candidates, int reps, int32_t* tasks_device,

@@ -116,8 +116,11 @@ extern "C" int lsefit_plan_autotune(const lsefit_batch* batch, const int64_t* of
     if (sms <= 0) return LSEFIT_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaStream_t cs = nullptr;  // private stream the candidates' fits are captured on
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
         (void)cudaGetLastError();
         return LSEFIT_ERR_CUDA;
     }
@@ -143,22 +146,38 @@ extern "C" int lsefit_plan_autotune(const lsefit_batch* batch, const int64_t* of
         hp.plan.block_tasks = tasks_device;
         hp.plan.warp_tasks = tasks_device + 4 * nb;
         rc = lsefit_fit_batched(batch, &hp.plan, X, nullptr, nullptr, nullptr, status, workspace, workspace_bytes,
-                                stream);  // warm-up
+                                stream);  // warm-up (also sets the kernel's attributes outside the capture)
         if (rc != LSEFIT_OK) break;
-        if (cudaEventRecord(e0, st) != cudaSuccess) {
+        // Time replays of the fit captured in a CUDA graph, the way a caller that
+        // replays graphs runs it: timed as plain back-to-back calls, the schedules
+        // can differ by less than the noise while their graph replays do not.
+        if (cudaStreamSynchronize(st) != cudaSuccess) {
             rc = LSEFIT_ERR_CUDA;
             break;
         }
-        for (int r = 0; r < reps && rc == LSEFIT_OK; ++r)
-            rc = lsefit_fit_batched(batch, &hp.plan, X, nullptr, nullptr, nullptr, status, workspace,
-                                    workspace_bytes, stream);
-        if (rc != LSEFIT_OK) break;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            rc = LSEFIT_ERR_CUDA;
+            break;
+        }
+        rc = lsefit_fit_batched(batch, &hp.plan, X, nullptr, nullptr, nullptr, status, workspace, workspace_bytes,
+                                (lsefit_stream_t)cs);
+        const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+        if (rc == LSEFIT_OK && (ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess))
+            rc = LSEFIT_ERR_CUDA;
         float ms = 0.0f;
-        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-            rc = LSEFIT_ERR_CUDA;
-            break;
+        if (rc == LSEFIT_OK) {
+            if (cudaGraphLaunch(exec, st) != cudaSuccess || cudaEventRecord(e0, st) != cudaSuccess) rc = LSEFIT_ERR_CUDA;
+            for (int r = 0; r < reps && rc == LSEFIT_OK; ++r)
+                if (cudaGraphLaunch(exec, st) != cudaSuccess) rc = LSEFIT_ERR_CUDA;
+            if (rc == LSEFIT_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = LSEFIT_ERR_CUDA;
         }
+        if (exec != nullptr) cudaGraphExecDestroy(exec);
+        if (graph != nullptr) cudaGraphDestroy(graph);
+        if (rc != LSEFIT_OK) break;
         ms /= (float)reps;
         if (ms_per_candidate != nullptr) ms_per_candidate[i] = ms;
         if (best_ms < 0.0f || ms < best_ms) {
@@ -169,6 +188,7 @@ extern "C" int lsefit_plan_autotune(const lsefit_batch* batch, const int64_t* of
     if (rc == LSEFIT_ERR_CUDA) (void)cudaGetLastError();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaStreamDestroy(cs);
     return rc;
 }
 

@@ -263,15 +263,19 @@ extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* 
     // schedule 3: blocks shared out over the degree classes in proportion to
     // their cost (points x relative time per point of the degree; block b starts
     // on the class holding (b + 1/2) / grid of the total).  Tasks of an invalid
-    // degree (class 0) are only marked, so they cost nothing.
+    // degree (class 0) are only marked, so they cost nothing -- unless class 0
+    // holds every task: a plan built without degrees, whose tasks are fitted,
+    // shares the blocks as for one class.
     {
         // time per point of the compensated FP32 ring at degree d relative to d = 1,
         // measured on GB300 with uniform batches (65,536 series of one degree)
         static const double kDegreeCost[kClasses] = {0.0, 1.00, 1.01, 1.05, 1.13, 1.29, 1.57, 1.86, 2.13};
-        double total = 0.0;
-        for (int c = 0; c < kClasses; ++c) total += (double)plan->class_points[c] * kDegreeCost[c];
+        double others = 0.0;
+        for (int c = 1; c < kClasses; ++c) others += (double)plan->class_points[c] * kDegreeCost[c];
+        const double cost0 = others > 0.0 ? 0.0 : 1.0;
+        const double total = (double)plan->class_points[0] * cost0 + others;
         int c = 0;
-        double cum = (double)plan->class_points[0] * kDegreeCost[0];
+        double cum = (double)plan->class_points[0] * cost0;
         p.cls_block[0] = 0;
         for (int64_t blk = 0; blk < grid; ++blk) {
             const double target = ((double)blk + 0.5) / (double)grid * total;
