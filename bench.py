@@ -536,7 +536,7 @@ def run_single_large(args, dist: Dist):
             e2e_mapped()
         torch.cuda.synchronize()
         dist.barrier()
-        _, em_total = _event_steps(e2e_mapped, e_steps, stream)
+        em_total = _event_steps(e2e_mapped, e_steps, stream)
         em_ms = dist.max(em_total)
         mapped_mode = {"value": dist.world * n * e_steps / (em_ms / 1e3), "ms_per_step": em_ms / e_steps,
                        "desc": "lsefit_fit on the pinned host buffers (the kernel reads host memory)"}
@@ -580,19 +580,18 @@ def run_single_large(args, dist: Dist):
 # shared timing helpers for the batched workloads
 # ---------------------------------------------------------------------------
 def _event_steps(step, steps, stream):
-    """Per-step CUDA-event durations (ms) and the total (ms) of `steps` calls of step()."""
+    """Device time (ms) of `steps` back-to-back calls of step(), between one pair of
+    CUDA events on `stream`.  (An event pair around every call adds about 4 us per
+    step: the records separate consecutive graph launches.)"""
     import torch
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    for a, b in evs:
-        a.record(stream)
+    for _ in range(steps):
         step()
-        b.record(stream)
     t1.record(stream)
     torch.cuda.synchronize()
-    return [a.elapsed_time(b) for a, b in evs], t0.elapsed_time(t1)
+    return t0.elapsed_time(t1)
 
 
 def _graph(fn, stream):
@@ -720,11 +719,11 @@ def run_ragged_batch(args, dist: Dist):
     clocks.start()
     dist.barrier()
     torch.cuda.synchronize()
-    per, total = _event_steps(g.replay, args.steps, stream)
+    total = _event_steps(g.replay, args.steps, stream)
     dist.barrier()
     clk = clocks.stop()
     ms = dist.max(total)
-    step_ms = dist.max(statistics.mean(per))
+    step_ms = dist.max(total / args.steps)
     per_series_bytes = 8 + 4 + 16 + 8 * (m_max + 1) + 4
     algo = 8 * N + per_series_bytes * S
 
@@ -783,8 +782,8 @@ def run_ragged_batch(args, dist: Dist):
         coef = coef_err_batched(b, fwd_full, pick, args.basis, args.accum)
         coef["timed_result_identical"] = same
     assert bool(torch.isfinite(res_out["sse"]).all())
-    rper, _ = _event_steps(lambda: L.residuals_batched(x, y, off, deg, fwd_full), args.steps, stream)
-    r_ms = dist.max(statistics.mean(rper))
+    rtot = _event_steps(lambda: L.residuals_batched(x, y, off, deg, fwd_full), args.steps, stream)
+    r_ms = dist.max(rtot / args.steps)
     cheb = args.basis != "monomial"
     residuals = {"ms_per_step": r_ms, "hbm_gbs": 8 * N / (r_ms / 1e3) / 1e9,
                  "roofline": _roofline(8 * N, r_ms,
@@ -805,7 +804,7 @@ def run_ragged_batch(args, dist: Dist):
 
         e2e_step()
         torch.cuda.synchronize()
-        _, e_total = _event_steps(e2e_step, 3, stream)
+        e_total = _event_steps(e2e_step, 3, stream)
         e_ms = dist.max(e_total) / 3
         e2e = {"value": dist.world * N / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": 8 * N,
                "d2h_bytes_per_step": 8 * (m_max + 1) * S, "ms_per_step": e_ms}
@@ -908,14 +907,14 @@ def run_diff_batch(args, dist: Dist):
     clocks.start()
     dist.barrier()
     torch.cuda.synchronize()
-    perf, totf = _event_steps(gf.replay, args.steps, stream)
+    totf = _event_steps(gf.replay, args.steps, stream)
     dist.barrier()
     clk_f = clocks.stop()
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     dist.barrier()
     torch.cuda.synchronize()
-    perb, totb = _event_steps(gb.replay, args.steps, stream)
+    totb = _event_steps(gb.replay, args.steps, stream)
     dist.barrier()
     clk = clocks.stop()
     msf = dist.max(totf) / args.steps
@@ -1016,7 +1015,7 @@ def run_diff_batch(args, dist: Dist):
 
         e2e_step()
         torch.cuda.synchronize()
-        _, e_total = _event_steps(e2e_step, 3, stream)
+        e_total = _event_steps(e2e_step, 3, stream)
         e_ms = dist.max(e_total) / 3
         e2e = {"value": dist.world * N / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": 8 * N,
                "d2h_bytes_per_step": 8 * N, "ms_per_step": e_ms}
@@ -1075,8 +1074,8 @@ def run_solve(args, dist: Dist):
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
-        per, total = _event_steps(step, args.steps, stream)
-        res[method] = {"ms": dist.max(statistics.mean(per)), "Xt": Xt.clone(), "status": st.clone()}
+        total = _event_steps(step, args.steps, stream)
+        res[method] = {"ms": dist.max(total / args.steps), "Xt": Xt.clone(), "status": st.clone()}
     clk = clocks.stop()
     both = ok & (res["gauss"]["status"] == 0) & (res["cholesky"]["status"] == 0)
     a, c = res["gauss"]["Xt"][both], res["cholesky"]["Xt"][both]
@@ -1147,7 +1146,7 @@ def run_single_fp64(args, dist: Dist):
     clocks.start()
     dist.barrier()
     torch.cuda.synchronize()
-    per, total = _event_steps(g.replay, args.steps, stream)
+    total = _event_steps(g.replay, args.steps, stream)
     dist.barrier()
     clk = clocks.stop()
     ms = dist.max(total) / args.steps
@@ -1240,13 +1239,13 @@ def run_general(args, dist: Dist):
     clocks.start()
     dist.barrier()
     torch.cuda.synchronize()
-    per, total = _event_steps(step, args.steps, stream)
+    total = _event_steps(step, args.steps, stream)
     dist.barrier()
     clk = clocks.stop()
     timed = {k: out[k].cpu().numpy() for k in ("X", "Xb")}
     timed_status = L.status_names(out["status"])[m - 1]
     ms_max = dist.max(total)
-    kern_ms = dist.max(statistics.mean(per))
+    kern_ms = dist.max(total / args.steps)
     streams = 3 if weighted else 2
     algo_bytes = 4 * streams * n
 
@@ -1267,7 +1266,7 @@ def run_general(args, dist: Dist):
             e2e_step()
         torch.cuda.synchronize()
         dist.barrier()
-        _, e_total = _event_steps(e2e_step, e_steps, stream)
+        e_total = _event_steps(e2e_step, e_steps, stream)
         e_ms = dist.max(e_total)
         copy_mode = {"value": dist.world * n * e_steps / (e_ms / 1e3), "ms_per_step": e_ms / e_steps}
 
@@ -1279,7 +1278,7 @@ def run_general(args, dist: Dist):
             e2e_mapped()
         torch.cuda.synchronize()
         dist.barrier()
-        _, em_total = _event_steps(e2e_mapped, e_steps, stream)
+        em_total = _event_steps(e2e_mapped, e_steps, stream)
         em_ms = dist.max(em_total)
         mapped_mode = {"value": dist.world * n * e_steps / (em_ms / 1e3), "ms_per_step": em_ms / e_steps}
         best = mapped_mode if mapped_mode["value"] > copy_mode["value"] else copy_mode

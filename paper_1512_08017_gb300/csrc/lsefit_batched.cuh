@@ -498,14 +498,6 @@ __device__ __noinline__ void pend_solve_entry(const BParams& p, unsigned char* p
         m = sid[32 + idx];
         s = sid[idx];
         const int ns = 3 * m + 2;
-        sm = reinterpret_cast<double*>(row);
-        sm[0] = (double)(long long)row[0];
-        if (ACC != LSEFIT_ACCUM_F64) {
-            for (int k = 1; k < ns; ++k) {
-                const dflt v = bits_df(row[k]);
-                sm[k] = f32_to_f64_int(v.hi) + f32_to_f64_int(v.lo);
-            }
-        }
         if (ACC == LSEFIT_ACCUM_F64) {
             ok = load_map_f64(p, s, c, sc);
         } else {
@@ -514,6 +506,27 @@ __device__ __noinline__ void pend_solve_entry(const BParams& p, unsigned char* p
             c = f32_to_f64_int(cf);
             sc = f32_to_f64_int(sf);
         }
+        // the sums output (monomial basis) is stored as the sums are converted,
+        // so that its stores drain during the elimination; the Chebyshev moments
+        // are only final after the solve's fix-up and are stored there
+        const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+        const int stride = 3 * p.m_max + 2;
+        double* so = (!CHEB && p.sums) ? p.sums + s * stride : nullptr;
+        sm = reinterpret_cast<double*>(row);
+        sm[0] = (double)(long long)row[0];
+        if (so) so[0] = ok ? sm[0] : qnan;
+        if (ACC != LSEFIT_ACCUM_F64) {
+            for (int k = 1; k < ns; ++k) {
+                const dflt v = bits_df(row[k]);
+                const double d = f32_to_f64_int(v.hi) + f32_to_f64_int(v.lo);
+                sm[k] = d;
+                if (so) so[k] = ok ? d : qnan;
+            }
+        } else if (so) {
+            for (int k = 1; k < ns; ++k) so[k] = ok ? sm[k] : qnan;
+        }
+        if (so)
+            for (int k = ns; k < stride; ++k) so[k] = 0.0;
     }
     // the solve is sized for the largest degree among the lanes solving together
     // (FP64 instructions cost the same for 1 or 32 lanes; padding does not), and
@@ -568,7 +581,7 @@ __device__ __noinline__ void pend_solve_entry(const BParams& p, unsigned char* p
             break;
     }
     p.status[s] = st;
-    if (p.sums) {
+    if (CHEB && p.sums) {
         const double qnan = __longlong_as_double(0x7ff8000000000000ll);
         const int stride = 3 * p.m_max + 2;
         const int ns = 3 * m + 2;
