@@ -57,7 +57,7 @@ typedef struct CUstream_st* lsefit_stream_t;
 #define LSEFIT_MAX_DEGREE 8
 /* Highest degree of lsefit_fit_general in the Chebyshev basis with FP64 accumulation. */
 #define LSEFIT_MAX_DEGREE_CHEBYSHEV 16
-#define LSEFIT_ABI_VERSION 3
+#define LSEFIT_ABI_VERSION 4
 
 /* Return and status codes. */
 enum {
@@ -378,6 +378,23 @@ int lsefit_plan_build(const int64_t* offsets_host, const int32_t* degree_host, i
                       int m_max, const lsefit_tuning* tuning, int num_sms, lsefit_plan* plan,
                       int32_t* block_tasks_host, int64_t block_cap,
                       int32_t* warp_tasks_host, int64_t warp_cap);
+
+/*
+ * lsefit_plan_class_blocks -- the degree class each persistent block of
+ * lsefit_fit_batched starts on under schedule 3 (the same sharing the fit
+ * uses).  The `grid` blocks are shared out over the classes in proportion to
+ * each class's points times the relative time per point of its degree; block
+ * b starts on the class holding (b + 1/2) / grid of the total.  Class 0 (a
+ * degree outside 1..LSEFIT_MAX_DEGREE) costs nothing, unless it holds every
+ * point (a plan built without degrees): its blocks then cover the grid.  Host
+ * only; no GPU needed.
+ *  plan       host, from lsefit_plan_build.
+ *  grid       persistent blocks (> 0; lsefit_fit_batched uses at most one per SM).
+ *  cls_block  host int32[LSEFIT_MAX_DEGREE + 2], written: blocks
+ *             [cls_block[c], cls_block[c+1]) start on class c (none when equal).
+ * Returns LSEFIT_OK, or LSEFIT_ERR_INVALID_ARG for a NULL pointer or grid < 1.
+ */
+int lsefit_plan_class_blocks(const lsefit_plan* plan, int grid, int32_t* cls_block);
 
 /* Bytes of workspace lsefit_fit_batched needs for `plan`. */
 size_t lsefit_batched_workspace_size(const lsefit_plan* plan);

@@ -183,6 +183,36 @@ extern "C" size_t lsefit_batched_workspace_size(const lsefit_plan* plan) {
     return ws_pend_off(plan) + ws_pend_bytes(plan);
 }
 
+// Schedule 3: the persistent blocks shared out over the degree classes in
+// proportion to their cost (points x relative time per point of the degree;
+// block b starts on the class holding (b + 1/2) / grid of the total).  Tasks of
+// an invalid degree (class 0) are only marked, so they cost nothing -- unless
+// class 0 holds every point: a plan built without degrees, whose tasks are
+// fitted, shares the blocks as for one class.
+extern "C" int lsefit_plan_class_blocks(const lsefit_plan* plan, int grid, int32_t* cls_block) {
+    if (plan == nullptr || cls_block == nullptr || grid < 1) return LSEFIT_ERR_INVALID_ARG;
+    // time per point of the compensated FP32 ring at degree d relative to d = 1,
+    // measured on GB300 with uniform batches (65,536 series of one degree)
+    static const double kDegreeCost[kClasses] = {0.0, 1.00, 1.01, 1.05, 1.13, 1.29, 1.57, 1.86, 2.13};
+    double others = 0.0;
+    for (int c = 1; c < kClasses; ++c) others += (double)plan->class_points[c] * kDegreeCost[c];
+    const double cost0 = others > 0.0 ? 0.0 : 1.0;
+    const double total = (double)plan->class_points[0] * cost0 + others;
+    int c = 0;
+    double cum = (double)plan->class_points[0] * cost0;
+    cls_block[0] = 0;
+    for (int blk = 0; blk < grid; ++blk) {
+        const double target = ((double)blk + 0.5) / (double)grid * total;
+        while (c < kClasses - 1 && !(cum > target)) {
+            ++c;
+            cum += (double)plan->class_points[c] * kDegreeCost[c];
+            cls_block[c] = blk;
+        }
+    }
+    for (int k = c + 1; k <= kClasses; ++k) cls_block[k] = grid;
+    return LSEFIT_OK;
+}
+
 extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* plan, double* X,
                                   double* Xt, double* sums, double* map, int32_t* status,
                                   void* workspace, size_t workspace_bytes, lsefit_stream_t stream) {
@@ -260,32 +290,10 @@ extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* 
     const int64_t useful = (int64_t)plan->n_block_tasks + (plan->n_warp_tasks + kBWarps - 1) / kBWarps;
     if (useful < grid) grid = useful;
     if (grid < 1) grid = 1;
-    // schedule 3: blocks shared out over the degree classes in proportion to
-    // their cost (points x relative time per point of the degree; block b starts
-    // on the class holding (b + 1/2) / grid of the total).  Tasks of an invalid
-    // degree (class 0) are only marked, so they cost nothing -- unless class 0
-    // holds every task: a plan built without degrees, whose tasks are fitted,
-    // shares the blocks as for one class.
     {
-        // time per point of the compensated FP32 ring at degree d relative to d = 1,
-        // measured on GB300 with uniform batches (65,536 series of one degree)
-        static const double kDegreeCost[kClasses] = {0.0, 1.00, 1.01, 1.05, 1.13, 1.29, 1.57, 1.86, 2.13};
-        double others = 0.0;
-        for (int c = 1; c < kClasses; ++c) others += (double)plan->class_points[c] * kDegreeCost[c];
-        const double cost0 = others > 0.0 ? 0.0 : 1.0;
-        const double total = (double)plan->class_points[0] * cost0 + others;
-        int c = 0;
-        double cum = (double)plan->class_points[0] * cost0;
-        p.cls_block[0] = 0;
-        for (int64_t blk = 0; blk < grid; ++blk) {
-            const double target = ((double)blk + 0.5) / (double)grid * total;
-            while (c < kClasses - 1 && !(cum > target)) {
-                ++c;
-                cum += (double)plan->class_points[c] * kDegreeCost[c];
-                p.cls_block[c] = (int)blk;
-            }
-        }
-        for (int k = c + 1; k <= kClasses; ++k) p.cls_block[k] = (int)grid;
+        int32_t cb[kClasses + 1];
+        (void)lsefit_plan_class_blocks(plan, (int)grid, cb);
+        for (int c = 0; c <= kClasses; ++c) p.cls_block[c] = cb[c];
     }
     {
         const int pt = kPrepThreads;
@@ -295,8 +303,9 @@ extern "C" int lsefit_fit_batched(const lsefit_batch* batch, const lsefit_plan* 
         prep<<<(unsigned)pb, pt, 0, (cudaStream_t)stream>>>(p);
         if (cudaGetLastError() != cudaSuccess) return LSEFIT_ERR_CUDA;
     }
-    // the persistent kernel starts while the preparation runs: it loads its first
-    // task records, then waits for the preparation's map constants and counters
+    // the persistent kernel is launched while the preparation runs (programmatic
+    // dependent launch): its blocks wait for the map constants and counters
+    // before their first draw
     if (launch_after_prior(k, dim3((unsigned)grid), dim3(kBBlock), smem, (cudaStream_t)stream, p) != cudaSuccess) {
         (void)cudaGetLastError();
         return LSEFIT_ERR_CUDA;

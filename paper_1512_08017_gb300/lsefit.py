@@ -36,7 +36,7 @@ ERR_SCRATCH_LIMIT = 9
 
 F64, F32, BF16 = 0, 1, 2
 ACCUM = {"naive": 0, "comp": 1, "f64": 2}
-ABI_VERSION = 3  # LSEFIT_ABI_VERSION the structures below are laid out for
+ABI_VERSION = 4  # LSEFIT_ABI_VERSION the structures below are laid out for
 MAX_DEGREE = 8
 MAX_DEGREE_CHEBYSHEV = 16  # Chebyshev basis with FP64 accumulation
 
@@ -98,6 +98,7 @@ SIGNATURES = {
     "lsefit_fit_noalloc": (_INT, [_VP, _VP, _I64, _INT, _INT, _INT, _INT, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "lsefit_plan_build": (_INT, [_VP, _VP, _I64, _INT, _VP, _INT, _VP, _VP, _I64, _VP, _I64]),
     "lsefit_batched_workspace_size": (_SZ, [_VP]),
+    "lsefit_plan_class_blocks": (_INT, [_VP, _INT, _VP]),
     "lsefit_fit_batched": (_INT, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "lsefit_residuals_workspace_size": (_SZ, [_VP]),
     "lsefit_residuals": (_INT, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),

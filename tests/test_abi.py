@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_host_only_calls(L):
-    assert L.lib.lsefit_abi_version() == L.ABI_VERSION == 3
+    assert L.lib.lsefit_abi_version() == L.ABI_VERSION == 4
     assert L.status_string(L.OK) == "ok"
     assert "singular" in L.status_string(L.ERR_SINGULAR)
     for m in range(1, 9):

@@ -122,6 +122,71 @@ def test_degree_classes_without_degrees(B):
 
 
 
+def class_blocks(B, plan, grid):
+    cb = np.zeros(10, dtype=np.int32)
+    rc = B.lib.lsefit_plan_class_blocks(ctypes.byref(plan), grid, cb.ctypes.data_as(ctypes.c_void_p))
+    assert rc == B.OK
+    return cb
+
+
+def test_class_blocks_share_the_grid(B):
+    """Schedule 3's block sharing (lsefit_plan_class_blocks, the function the fit
+    calls): a partition of the grid into one block range per degree class, in
+    class order, that gives the blocks to the classes holding points."""
+    grid = 152
+    rng = np.random.default_rng(3)
+    lens = rng.integers(1, 20000, 3000)
+    off = np.concatenate([[0], np.cumsum(lens)])
+    deg = rng.integers(1, 6, lens.size)
+    rc, plan, _, _ = build(B, off, deg, warp_max_len=1 << 20)
+    assert rc == B.OK
+    cb = class_blocks(B, plan, grid)
+    assert cb[0] == 0 and cb[-1] == grid and np.all(np.diff(cb) >= 0)
+    counts = np.diff(cb)
+    assert counts[0] == 0 and np.all(counts[6:] == 0) and np.all(counts[1:6] > 0)
+    # shares follow the points: each class within two blocks of its share of the
+    # points times a cost per point that grows with the degree by at most 2.2x
+    pts = np.array([plan.class_points[c] for c in range(9)], dtype=float)
+    share = pts[1:6] / pts[1:6].sum() * grid
+    assert np.all(counts[1:6] >= np.floor(share / 2.2) - 2) and np.all(counts[1:6] <= np.ceil(share * 2.2) + 2)
+    # for equal points, a higher degree never gets fewer blocks
+    eq = np.concatenate([[0], np.cumsum(np.full(8 * 40, 1000))])
+    rc, plan, _, _ = build(B, eq, np.repeat(np.arange(1, 9), 40), m_max=8, warp_max_len=1 << 20)
+    cb = class_blocks(B, plan, grid)
+    assert np.all(np.diff(np.diff(cb)[1:9]) >= 0) and cb[1] == 0 and cb[9] == grid
+
+
+def test_class_blocks_single_class_and_invalid_degrees(B):
+    grid = 152
+    off = np.arange(0, 4097 * 4096, 4096)
+    # one degree: every block starts on its class
+    rc, plan, _, _ = build(B, off, np.full(4096, 3), m_max=3, warp_max_len=1 << 20)
+    assert list(class_blocks(B, plan, grid)) == [0, 0, 0, 0] + [grid] * 6
+    # tasks of an invalid degree are only marked: no block starts on class 0 ...
+    deg = np.full(4096, 3)
+    deg[:2000] = 0
+    rc, plan, _, _ = build(B, off, deg, m_max=3, warp_max_len=1 << 20)
+    assert plan.class_points[0] == 2000 * 4096
+    assert list(class_blocks(B, plan, grid)) == [0, 0, 0, 0] + [grid] * 6
+    # ... unless they are all there is: a plan built without degrees shares the
+    # grid as one class (before, its total cost was 0 and blocks started on
+    # empty classes)
+    rc, plan, _, _ = build(B, off, m_max=3, warp_max_len=1 << 20)
+    assert plan.class_points[0] == 4096 * 4096
+    assert list(class_blocks(B, plan, grid)) == [0] + [grid] * 9
+    rc, plan, _, _ = build(B, off, np.zeros(4096), m_max=3, warp_max_len=1 << 20)
+    assert list(class_blocks(B, plan, 7)) == [0] + [7] * 9
+
+
+def test_class_blocks_bad_arguments(B):
+    rc, plan, _, _ = build(B, [0, 10, 20], [1, 2])
+    cb = np.zeros(10, dtype=np.int32)
+    ptr = cb.ctypes.data_as(ctypes.c_void_p)
+    assert B.lib.lsefit_plan_class_blocks(ctypes.byref(plan), 0, ptr) == B.ERR_INVALID_ARG
+    assert B.lib.lsefit_plan_class_blocks(None, 152, ptr) == B.ERR_INVALID_ARG
+    assert B.lib.lsefit_plan_class_blocks(ctypes.byref(plan), 152, None) == B.ERR_INVALID_ARG
+
+
 def test_plan_records_a_common_warp_task_length(B):
     """warp_task_len: the length every warp task shares (the gradient pass then
     splits their points evenly over its warps), 0 when lengths differ."""
