@@ -2,7 +2,7 @@
 
 Forward error.  The coefficients are compared with the oracle's FP64 fit of
 the same stored points, in the mapped basis (normwise relative error of Xt).
-The bounds of the task are 1e-6 for FP64 accumulation and 1e-5 for
+The stated bounds are 1e-6 for FP64 accumulation and 1e-5 for
 compensated FP32 of degree <= 3 on [-1, 1].  Beyond that, a coefficient is
 only as well determined as the normal system allows: to first order its
 error is cond(A) times the relative perturbation of A and B.  So a forward
