@@ -134,3 +134,30 @@ def test_general_coefficient_record():
     assert bad["rel_Xb"] > 1e-5 and bad["rel_X"] > 1e-5 and bad["backward"] > 1e-6
     assert bench.coef_err_general(out, ref, 4, "f64", 5000, "singular") == {
         "degree": 4, "status": "singular", "oracle_status": "ok"}
+
+
+def test_timed_region_is_one_event_pair(monkeypatch):
+    """The K timed steps run back to back between one pair of events on the
+    launching stream (an event pair around every step separates consecutive graph
+    launches); the result is the pair's elapsed time."""
+    import torch
+    log = []
+
+    class FakeEvent:
+        def __init__(self, enable_timing=False):
+            assert enable_timing
+            self.at = None
+
+        def record(self, stream=None):
+            log.append(("record", stream))
+            self.at = len(log)
+
+        def elapsed_time(self, other):
+            return float(other.at - self.at)
+
+    monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: log.append(("sync",)))
+    stream = object()
+    total = bench._event_steps(lambda: log.append(("step",)), 7, stream)
+    assert log == [("record", stream)] + [("step",)] * 7 + [("record", stream), ("sync",)]
+    assert total == 8.0
